@@ -1,0 +1,161 @@
+"""Pins of the oracle's COCG / shifted COCG (Appendix) and dense G0 (Eq. GF4).
+
+* G0 at V=0 with the 2nd-order stencil equals the separable DST closed form
+  sum_modes phi phi^T / (Z - eps) (independent of the sparse assembly).
+* COCG and shifted COCG reproduce a dense LU solve (a library routine) to
+  well below the tolerance they were run at, for 2nd/4th order and with
+  projectors; seed switching is exercised and does not change the result.
+* The true residual b - (Z_i - H) x^(i) matches the collinear estimate
+  ||r_n|| / |pi_n^(i)| (Eq. collinear).
+* G0 is complex symmetric (G^T = G).
+* Planted mistakes (a conjugated bilinear form, a flipped shift sign, a
+  dropped r_{n-2} term) make the comparison with the dense solve fail.
+"""
+
+import numpy as np
+import pytest
+
+from workloads import small_problem
+from oracle import cocg as oc
+from oracle.operator import hamiltonian, apply_h, dense_hamiltonian, boundary_rows
+from oracle.dense import g0_dense
+
+
+def _dst_g0(p, Z):
+    nx, ny, nz = p.grid
+    h = p.h
+    def basis(n):
+        k = np.arange(1, n + 1)
+        i = np.arange(1, n + 1)
+        phi = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, k) * np.pi / (n + 1))   # [point, mode]
+        lam = (1.0 - np.cos(k * np.pi / (n + 1))) / h ** 2
+        return phi, lam
+    (px, lx), (py, ly), (pz, lz) = basis(nx), basis(ny), basis(nz)
+    Phi = np.kron(pz, np.kron(py, px))
+    lam = (lz[:, None, None] + ly[None, :, None] + lx[None, None, :]).ravel()
+    return (Phi / (Z - lam)[None, :]) @ Phi.T
+
+
+def test_dense_g0_matches_dst_closed_form():
+    p = small_problem(grid=(4, 3, 6), h=0.5, fd_order=2, n_wells=0)
+    Z = 0.9 + 0.05j
+    np.testing.assert_allclose(g0_dense(p, Z), _dst_g0(p, Z), atol=1e-12)
+
+
+def test_g0_complex_symmetric():
+    p = small_problem(grid=(4, 4, 6), fd_order=4, n_wells=2, projectors=1)
+    G = g0_dense(p, 0.5 + 0.01j)
+    assert np.abs(G - G.T).max() < 1e-12 * np.abs(G).max()
+    assert np.abs(G - G.conj().T).max() > 1e-3 * np.abs(G).max()     # not Hermitian
+
+
+@pytest.mark.parametrize("order,proj", [(2, 0), (4, 0), (4, 2)])
+def test_cocg_single_energy_matches_dense(order, proj):
+    p = small_problem(grid=(5, 4, 8), h=0.5, fd_order=order, n_wells=2, projectors=proj)
+    H, P, wE = hamiltonian(p)
+    Z = 0.7 + 0.02j
+    j = 3
+    b = np.zeros(p.N, complex)
+    b[j] = 1
+    x, it, st, hist = oc.cocg(lambda v: Z * v - apply_h(H, P, wE, v), b, 1e-12)
+    assert st == oc.OK and hist[-1] < 1e-12
+    xd = g0_dense(p, Z, cols=[j])[:, 0]
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+@pytest.mark.parametrize("order,proj,seed", [(2, 0, "mid"), (4, 0, "first"), (4, 2, "mid"), (2, 0, 5)])
+def test_shifted_matches_dense_and_single(order, proj, seed):
+    p = small_problem(grid=(5, 4, 8), h=0.5, fd_order=order, n_wells=2, projectors=proj, n_energies=6,
+                      e_range=(-0.5, 2.5), eta=2e-2)
+    H, P, wE = hamiltonian(p)
+    Z = p.energies + 1j * p.eta
+    j = 7
+    b = np.zeros(p.N, complex)
+    b[j] = 1
+    r = oc.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-12, seed=seed)
+    assert r.status == oc.OK
+    for k in range(Z.size):
+        xd = g0_dense(p, Z[k], cols=[j])[:, 0]
+        assert np.linalg.norm(r.x[k] - xd) / np.linalg.norm(xd) < 1e-9, k
+        xs, _, st, _ = oc.cocg(lambda v: Z[k] * v - apply_h(H, P, wE, v), b, 1e-12)
+        assert np.linalg.norm(r.x[k] - xs) / np.linalg.norm(xs) < 1e-9
+        # true residual vs the collinear estimate
+        tr = np.linalg.norm(b - (Z[k] * r.x[k] - apply_h(H, P, wE, r.x[k])))
+        assert tr < 50 * 1e-12 and r.final_res[k] < 1e-12
+
+
+def test_seed_switching_exercised_and_invariant():
+    # the seed sits far below the spectrum, converges first and must be switched away from
+    p = small_problem(grid=(5, 4, 8), h=0.5, fd_order=4, n_wells=2, n_energies=5, eta=1e-2)
+    H, P, wE = hamiltonian(p)
+    Z = np.array([-6.0, 0.3, 0.8, 1.4, 3.0]) + 1j * p.eta
+    b = np.zeros(p.N, complex)
+    b[11] = 1
+    r0 = oc.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-12, seed=0)
+    assert r0.switches >= 1 and r0.status == oc.OK
+    r1 = oc.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-12, seed=2)
+    for k in range(Z.size):
+        xd = g0_dense(p, Z[k], cols=[11])[:, 0]
+        for r in (r0, r1):
+            assert np.linalg.norm(r.x[k] - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_columns_and_rows_restriction():
+    p = small_problem(grid=(4, 4, 6), h=0.5, fd_order=2, n_wells=1, n_energies=3, eta=5e-2)
+    rows = boundary_rows(p.grid, 1)
+    G, res = oc.shifted_cocg_columns(p)
+    assert G.shape == (3, rows.size, p.cols.size)
+    for k, E in enumerate(p.energies):
+        Gd = g0_dense(p, E + 1j * p.eta, rows=rows, cols=p.cols)
+        assert np.linalg.norm(G[k] - Gd) / np.linalg.norm(Gd) < 1e-9
+        # boundary block of a symmetric matrix with rows == cols is symmetric
+        assert np.abs(G[k] - G[k].T).max() < 1e-9 * np.abs(G[k]).max()
+
+
+def _shifted_err(p, patched):
+    H, P, wE = hamiltonian(p)
+    Z = p.energies + 1j * p.eta
+    b = np.zeros(p.N, complex)
+    b[5] = 1
+    r = oc.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-10, maxit=2000)
+    errs = []
+    for k in range(Z.size):
+        xd = g0_dense(p, Z[k], cols=[5])[:, 0]
+        errs.append(np.linalg.norm(r.x[k] - xd) / np.linalg.norm(xd))
+    return max(errs)
+
+
+@pytest.mark.parametrize("mistake", ["conjugated_form", "flipped_shift"])
+def test_planted_mistakes_are_caught(monkeypatch, mistake):
+    p = small_problem(grid=(4, 4, 6), h=0.5, fd_order=2, n_wells=2, n_energies=4, eta=3e-2)
+    assert _shifted_err(p, None) < 1e-8
+    if mistake == "conjugated_form":
+        monkeypatch.setattr(oc, "bilinear", lambda x, y: np.vdot(x, y))
+    else:
+        orig = oc.shifted_cocg
+
+        def flipped(apply_H, b, Z, tol, **kw):
+            # solving (Z_s - H) with shifts of the wrong sign == energies mirrored about the seed
+            Zs = Z[Z.size // 2]
+            return orig(apply_H, b, 2 * Zs - Z + 2j * Z.imag, tol, **kw)
+        monkeypatch.setattr(oc, "shifted_cocg", flipped)
+    assert _shifted_err(p, mistake) > 1e-4
+
+
+def test_chain_shifted_dyson_transmission_matches_dense():
+    """G0_bb by shifted COCG -> Dyson -> T equals T from the dense Eq. GF2 (full oracle chain)."""
+    from oracle.leads import sigma_bloch
+    from oracle.dense import g_dense
+    from oracle.dyson import dyson_solve
+    from oracle.transmission import transmission
+    p = small_problem(grid=(4, 3, 8), h=0.5, fd_order=4, n_wells=2, projectors=1, n_energies=4,
+                      e_range=(1.0, 4.0), eta=1e-2)
+    b = boundary_rows(p.grid, p.n_face)
+    G0, res = oc.shifted_cocg_columns(p, cols=b, rows=b)
+    for k, E in enumerate(p.energies):
+        Z = E + 1j * p.eta
+        SL, SR = sigma_bloch(4, 3, p.h, 4, Z)
+        G = dyson_solve(G0[k], SL, SR)
+        Gd = g_dense(p, Z, SL, SR, rows=b, cols=b)
+        assert np.linalg.norm(G - Gd) / np.linalg.norm(Gd) < 1e-9
+        assert abs(transmission(G, SL, SR)[0] - transmission(Gd, SL, SR)[0]) < 1e-9
