@@ -1,0 +1,201 @@
+/*
+ * rsfd.h -- C ABI of the GB300 shifted-COCG / Dyson transport library.
+ *
+ * The library computes, for a transition region discretised on a real-space
+ * finite-difference (RSFD) grid,
+ *
+ *   1. the unperturbed boundary Green's function  G0_bb(Z_k) = [(Z_k - H_T)^{-1}]_{b,cols}
+ *      for every complex energy Z_k = E_k + i*eta and every right-hand side e_j,
+ *      by the shifted COCG method with seed switching (paper: Sec. III B, Eq. GF4,
+ *      Appendix Eqs. Eq ... seedswitch);
+ *   2. the perturbed boundary Green's function G_bb from G0_bb and the lead
+ *      self-energies through the exact OBM/Dyson relation (Eq. sec3-01a,
+ *      Eqs. sec3-02 ... sec3-06);
+ *   3. the Fisher-Lee transmission T(E) (Eq. TF).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: Nx x Ny x Nz points, spacing h (bohr), z = transport direction.  A point
+ *   (x, y, z) has linear index (z*Ny + y)*Nx + x.  H_T = -1/2 nabla^2 + V_loc
+ *   (+ nonlocal projectors) with central finite differences of order 2 (7-point)
+ *   or 4 (13-point) and zero ghosts outside the box on all six faces (the leads
+ *   enter only through the self-energies).  Hartree atomic units.
+ * Boundary row set b: the n_face outermost z-planes on each side, in increasing
+ *   z, each plane x fastest; nb = 2*n_face*Nx*Ny.  The first half of b is the
+ *   left slab, the second half the right slab; ns = nb/2.
+ * Complex numbers: interleaved (re, im).  "c64" = 2 x float, "c128" = 2 x double.
+ *   The handle's precision picks the element type of G0_bb / G_bb: c128 for
+ *   RSFD_FP64, c64 for RSFD_MIXED.
+ * Matrices: column-major per energy.  G0_bb is [K][ncols][nb]: element
+ *   (k, row r, column c) sits at k*nb*ncols + c*nb + r.  Self-energies are
+ *   [K][ns][ns] c128 with element (k, a, c) at k*ns*ns + c*ns + a.
+ * Memory ownership: the caller owns every input and output buffer; "device"
+ *   buffers must be device memory of the current CUDA device, "host" buffers
+ *   host memory.  The handle owns its internal work buffers (allocated lazily,
+ *   grown on demand, freed by rsfd_destroy).
+ * Streams: every device operation is issued on the stream given to rsfd_create
+ *   (a cudaStream_t passed as void*; NULL = legacy default stream).  Calls that
+ *   return host results synchronise that stream before returning.
+ * Errors: no C++ exception crosses this ABI.  Each call returns an rsfd_status;
+ *   the message of the last failure is available from rsfd_last_error().  A
+ *   CUDA error inside a call returns RSFD_ERR_CUDA.  Per-column solver outcomes
+ *   (not converged, breakdown) are reported in rsfd_col_info and the call
+ *   returns the worst of them.
+ * Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef RSFD_H
+#define RSFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsfd_handle_s* rsfd_handle;
+
+typedef enum {
+  RSFD_OK = 0,
+  RSFD_ERR_ARG = 1,           /* invalid argument (message says which) */
+  RSFD_ERR_ALLOC = 2,         /* device or host allocation failed */
+  RSFD_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  RSFD_ERR_NOT_CONVERGED = 4, /* some column hit maxit before every energy converged */
+  RSFD_ERR_BREAKDOWN = 5,     /* COCG breakdown: (r, r) quasi-null while r != 0 */
+  RSFD_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  RSFD_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
+} rsfd_status;
+
+typedef enum { RSFD_FP64 = 0, RSFD_MIXED = 1 } rsfd_precision;
+
+/* Initial seed of the shifted COCG (Appendix; Sec. III C starts from the Fermi energy). */
+typedef enum {
+  RSFD_SEED_MID = 0,   /* energy index K/2 */
+  RSFD_SEED_FIRST = 1, /* energy index 0 */
+  RSFD_SEED_INDEX = 2  /* energy index seed_index */
+} rsfd_seed_kind;
+
+/* Separable nonlocal projectors, one per atom (Sec. II A mentions nonlocal
+ * pseudopotentials as an extension): V_nl psi = sum_a E_a p_a (p_a^T psi) h^3.
+ * CSR over atoms; all arrays are host memory, copied by rsfd_create. */
+typedef struct {
+  int32_t n_atoms;
+  const int64_t* ptr; /* [n_atoms + 1] */
+  const int64_t* idx; /* [nnz] linear grid indices */
+  const double* val;  /* [nnz] projector values p_a(r_j) */
+  const double* E;    /* [n_atoms] projector energies (Hartree) */
+} rsfd_projectors;
+
+/* Outcome of one right-hand side column of rsfd_shifted_cocg. */
+typedef struct {
+  int32_t iters;      /* seed iterations = applications of H_T */
+  int32_t switches;   /* seed switches (Eq. seedswitch) */
+  int32_t status;     /* RSFD_OK, RSFD_ERR_NOT_CONVERGED or RSFD_ERR_BREAKDOWN */
+  int32_t final_seed; /* energy index of the seed when the column finished */
+} rsfd_col_info;
+
+/* Launch options of the solver; zero fields mean "choose automatically". */
+typedef struct {
+  int32_t slots;          /* columns iterated together (RHS block width) */
+  int32_t iters_per_sync; /* iterations per CUDA-graph replay between host checks */
+  int32_t tile_y;         /* stencil tile height in y; (32+2*fd_order)*(tile_y+2*fd_order) must be a
+                             multiple of 32 and <= 640 (RSFD_ERR_ARG otherwise) */
+  int32_t z_chunk;        /* planes per CTA along z */
+  int32_t use_graphs;     /* 1 = capture iteration chunks in CUDA graphs (default), -1 = plain launches */
+  int32_t profile;        /* 1 = time every kernel launch with CUDA events (rsfd_get_stats) */
+} rsfd_solve_opts;
+
+/* Counters of the last rsfd_shifted_cocg call. */
+typedef struct {
+  double ms_total;            /* wall time of the call on the device stream (events) */
+  double ms_pass;             /* summed duration of stencil/seed-update launches (profile = 1) */
+  double ms_shift;            /* summed duration of shift-update launches (profile = 1) */
+  int64_t n_pass;             /* stencil/seed-update launches */
+  int64_t n_shift;            /* shift-update launches */
+  int64_t n_other;            /* other kernel launches (slot set-up, reductions) */
+  int64_t slot_iterations;    /* sum over columns of seed iterations */
+  int64_t shift_updates;      /* sum over iterations of active (column, energy) pairs */
+  int32_t slots;              /* columns in flight that were used */
+  int32_t iters_per_sync;
+} rsfd_stats;
+
+/* Create a handle for one transition region (Sec. II A, Eq. sabun1).
+ *   grid[3]   = {Nx, Ny, Nz}, each >= 1 (host).
+ *   h         > 0, grid spacing.
+ *   fd_order  = 2 or 4.
+ *   n_face    = planes per side in the boundary row set b, 1 <= n_face <= Nz/2;
+ *               0 selects fd_order/2 (the planes the lead couples to).
+ *   V_loc     = host [N] local potential, linear grid order.
+ *   proj      = NULL or the nonlocal projectors (host arrays, copied).
+ *   precision = RSFD_FP64 or RSFD_MIXED.
+ *   stream    = cudaStream_t for every device operation of this handle.
+ * Returns RSFD_ERR_ARG on invalid sizes, RSFD_ERR_ALLOC / RSFD_ERR_CUDA on
+ * device failures; *out is NULL unless RSFD_OK. */
+rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double h, int32_t fd_order, int32_t n_face,
+                        const double* V_loc, const rsfd_projectors* proj, int32_t precision, void* stream);
+
+/* The boundary row set b (linear grid indices).  *nb receives its size; rows may
+ * be NULL (size query) or a host array of at least *nb entries. */
+rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows);
+
+/* Set launch options for later solves (NULL restores the defaults). */
+rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* opts);
+
+/* Shifted COCG with seed switching (Sec. III B; Appendix):
+ *   (Z_k - H_T) x^(k) = e_j  for k < K and every column j in cols,
+ * keeping only the rows b of every x^(k):  G0_bb[k][:, c] = x^(k)_b for j = cols[c].
+ *   cols       host [ncols] linear grid indices of the unit right-hand sides.
+ *   energies   host [K] real parts E_k; Z_k = E_k + i*eta, eta > 0.
+ *   tol        convergence threshold on ||r^(k)||_2 / ||e_j||_2 for every k.
+ *   maxit      iteration cap per column (>= 1).
+ *   seed_kind  rsfd_seed_kind; seed_index used with RSFD_SEED_INDEX.
+ *   G0_bb      device output [K][ncols][nb], c64 or c128 per the handle's precision.
+ *   info       host output [ncols] (nullable).
+ *   final_res  host output [ncols][K] residual of each energy at exit (nullable).
+ * Synchronises the handle's stream.  Returns RSFD_OK when every column
+ * converged, else the worst per-column status. */
+rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+                              double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
+                              void* G0_bb, rsfd_col_info* info, double* final_res);
+
+/* Counters and timings of the last rsfd_shifted_cocg call on this handle. */
+rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out);
+
+/* Dyson / OBM boundary step (Eq. sec3-01a restricted to b):
+ *   (I - G0_bb(k) Sigma_bb(k)) G_bb(k) = G0_bb(k),  Sigma_bb = diag(Sigma_L, Sigma_R),
+ * for every k < K.  G0_bb must hold all boundary columns in b order
+ * (ncols = nb).  The solve is an LU with partial pivoting followed by FP64
+ * iterative refinement of the residual G0 - (I - G0 Sigma) G.
+ *   G0_bb    device [K][nb][nb] (handle precision).
+ *   Sigma_L, Sigma_R  device [K][ns][ns] c128.
+ *   G_bb     device output, same layout and type as G0_bb (may not alias G0_bb).
+ *   refine_residual  host [K] (nullable): ||G0 - M G||_F / ||G0||_F after refinement. */
+rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+                                int32_t K, void* G_bb, double* refine_residual);
+
+/* Fisher-Lee transmission (Eq. TF; Gamma = i(Sigma - Sigma^dag)):
+ *   T(k) = Tr[Gamma_L G_RL^dag Gamma_R G_RL],  G_RL = G_bb(k)[right slab, left slab].
+ *   G_bb  device [K][nb][nb] (handle precision);  Sigma_L, Sigma_R device [K][ns][ns] c128;
+ *   T     host output [K]. */
+rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                              double* T);
+
+/* Self-energies of uniform V=0 leads that continue the grid (same Nx, Ny, h,
+ * fd_order, Dirichlet walls) on both sides (Eqs. self-energy, sec2-01, sec2-02),
+ * computed on the host in FP64 from the outgoing Bloch roots of each
+ * transverse mode.  ns = (fd_order/2)*Nx*Ny.
+ *   energies host [K];  Sigma_L, Sigma_R host outputs [K][ns][ns] c128 (interleaved doubles). */
+rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double h, int32_t fd_order, const double* energies,
+                                    double eta, int32_t K, double* Sigma_L, double* Sigma_R);
+
+/* Message of the last failure on this handle (h = NULL: last failure of a call
+ * without a handle, e.g. rsfd_create).  Never NULL. */
+const char* rsfd_last_error(rsfd_handle h);
+
+/* Free the handle and its device buffers (synchronises its stream).  NULL is a no-op. */
+void rsfd_destroy(rsfd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSFD_H */

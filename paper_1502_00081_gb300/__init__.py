@@ -1,0 +1,21 @@
+"""GB300 shifted-COCG / Dyson transport library: Python binding of the C ABI in ``include/rsfd.h``.
+
+Every function here only marshals arguments (numpy host arrays, torch device
+tensors, the current CUDA stream) into the C entry points of ``librsfd.so``;
+all arithmetic of the method runs in the library's CUDA kernels (or, for the
+lead self-energy helper, in its host C++).  There is no Python or CPU
+fallback: importing the binding fails if the library has not been built.
+
+Paper: S. Iwase, T. Hoshi, T. Ono, "Efficient numerical solver for
+first-principles transport calculation based on real-space finite-difference
+method" -- shifted COCG for the unperturbed Green's functions (Sec. III B,
+Appendix) and the OBM/Dyson relation to the perturbed ones (Eq. sec3-01a).
+"""
+
+from .binding import (  # noqa: F401
+    RSFD_OK, RSFD_FP64, RSFD_MIXED, RSFD_SEED_MID, RSFD_SEED_FIRST, RSFD_SEED_INDEX,
+    RsfdError, lib_path, load_library,
+    rsfd_create, rsfd_boundary_rows, rsfd_set_solve_options, rsfd_shifted_cocg, rsfd_get_stats,
+    rsfd_dyson_boundary, rsfd_transmission, rsfd_lead_sigma_uniform, rsfd_last_error, rsfd_destroy,
+    Handle,
+)

@@ -1,0 +1,285 @@
+"""ctypes binding of ``librsfd.so`` (argument marshalling only).
+
+Host inputs are numpy arrays; device buffers are torch CUDA tensors whose
+``data_ptr()`` is passed through.  Matrices follow the C ABI's column-major
+convention per energy: a torch tensor ``G`` of shape ``(K, ncols, nb)`` holds
+column ``c`` of energy ``k`` in ``G[k, c, :]`` (so ``G[k].T`` is the matrix).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+RSFD_OK = 0
+RSFD_ERR_ARG = 1
+RSFD_ERR_ALLOC = 2
+RSFD_ERR_CUDA = 3
+RSFD_ERR_NOT_CONVERGED = 4
+RSFD_ERR_BREAKDOWN = 5
+RSFD_ERR_TIMEOUT = 6
+RSFD_ERR_UNSUPPORTED = 7
+RSFD_FP64 = 0
+RSFD_MIXED = 1
+RSFD_SEED_MID = 0
+RSFD_SEED_FIRST = 1
+RSFD_SEED_INDEX = 2
+
+_STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED", 5: "ERR_BREAKDOWN",
+           6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+
+
+class RsfdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class rsfd_projectors(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("idx", ctypes.POINTER(ctypes.c_int64)), ("val", ctypes.POINTER(ctypes.c_double)),
+                ("E", ctypes.POINTER(ctypes.c_double))]
+
+
+class rsfd_col_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("switches", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("final_seed", ctypes.c_int32)]
+
+
+class rsfd_solve_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class rsfd_stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double), ("ms_shift", ctypes.c_double),
+                ("n_pass", ctypes.c_int64), ("n_shift", ctypes.c_int64), ("n_other", ctypes.c_int64),
+                ("slot_iterations", ctypes.c_int64), ("shift_updates", ctypes.c_int64),
+                ("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32)]
+
+
+# every symbol declared in include/rsfd.h, with (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "rsfd_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(rsfd_projectors), ctypes.c_int32, _P]),
+    "rsfd_boundary_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    "rsfd_set_solve_options": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_solve_opts)]),
+    "rsfd_shifted_cocg": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                         ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
+    "rsfd_dyson_boundary": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_transmission": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_lead_sigma_uniform": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_last_error": (ctypes.c_char_p, [_P]),
+    "rsfd_destroy": (None, [_P]),
+}
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "librsfd.so")
+
+
+def load_library():
+    """Load librsfd.so (raises if it has not been built; there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        p = lib_path()
+        if not os.path.exists(p):
+            raise ImportError(f"{p} is missing: build it with paper_1502_00081_gb300.build_lib.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(h, status, allow=()):
+    if status != RSFD_OK and status not in allow:
+        raise RsfdError(status, rsfd_last_error(h))
+    return status
+
+
+def _dev_ptr(t, dtypes, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def rsfd_last_error(h=None) -> str:
+    return load_library().rsfd_last_error(h).decode()
+
+
+def rsfd_create(grid, h, fd_order, V_loc, n_face=0, proj=None, precision=RSFD_FP64, stream=None):
+    lib = load_library()
+    g = (ctypes.c_int32 * 3)(*[int(v) for v in grid])
+    V, Vp = _f64(np.asarray(V_loc).ravel())
+    keep = []
+    pp = None
+    if proj is not None:
+        ptr, ptrp = _i64(proj.ptr)
+        idx, idxp = _i64(proj.idx)
+        val, valp = _f64(proj.val)
+        E, Ep = _f64(proj.E)
+        keep += [ptr, idx, val, E]
+        pp = ctypes.byref(rsfd_projectors(int(proj.n_atoms), ptrp, idxp, valp, Ep))
+    out = ctypes.c_void_p()
+    st = lib.rsfd_create(ctypes.byref(out), g, float(h), int(fd_order), int(n_face), Vp, pp, int(precision),
+                         _stream_ptr(stream))
+    _check(None, st)
+    return out
+
+
+def rsfd_boundary_rows(h):
+    lib = load_library()
+    nb = ctypes.c_int32()
+    _check(h, lib.rsfd_boundary_rows(h, ctypes.byref(nb), None))
+    rows = np.zeros(nb.value, np.int64)
+    _check(h, lib.rsfd_boundary_rows(h, ctypes.byref(nb), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return rows
+
+
+def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0):
+    lib = load_library()
+    o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile))
+    _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
+
+
+def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_SEED_MID, seed_index=0):
+    """Returns (status, info [ncols] structured array, final_res [ncols, K])."""
+    import torch
+    lib = load_library()
+    c, cp = _i64(cols)
+    e, ep = _f64(energies)
+    ptr = _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
+    info = (rsfd_col_info * c.size)()
+    res = np.zeros((c.size, e.size), np.float64)
+    st = lib.rsfd_shifted_cocg(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
+                               int(seed_kind), int(seed_index), ptr, info,
+                               res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(h, st, allow=(RSFD_ERR_NOT_CONVERGED, RSFD_ERR_BREAKDOWN))
+    arr = np.array([(i.iters, i.switches, i.status, i.final_seed) for i in info],
+                   dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
+                          ("final_seed", np.int32)])
+    return st, arr, res
+
+
+def rsfd_get_stats(h) -> dict:
+    lib = load_library()
+    s = rsfd_stats()
+    _check(h, lib.rsfd_get_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in rsfd_stats._fields_}
+
+
+def rsfd_dyson_boundary(h, G0_bb, Sigma_L, Sigma_R, G_bb):
+    import torch
+    lib = load_library()
+    K = int(G0_bb.shape[0])
+    p0 = _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
+    pl = _dev_ptr(Sigma_L, (torch.complex128,), name="Sigma_L")
+    pr = _dev_ptr(Sigma_R, (torch.complex128,), name="Sigma_R")
+    pg = _dev_ptr(G_bb, (G0_bb.dtype,), tuple(G0_bb.shape), name="G_bb")
+    ref = np.zeros(K, np.float64)
+    _check(h, lib.rsfd_dyson_boundary(h, p0, pl, pr, K, pg, ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return ref
+
+
+def rsfd_transmission(h, G_bb, Sigma_L, Sigma_R):
+    import torch
+    lib = load_library()
+    K = int(G_bb.shape[0])
+    pg = _dev_ptr(G_bb, (torch.complex64, torch.complex128), name="G_bb")
+    pl = _dev_ptr(Sigma_L, (torch.complex128,), name="Sigma_L")
+    pr = _dev_ptr(Sigma_R, (torch.complex128,), name="Sigma_R")
+    T = np.zeros(K, np.float64)
+    _check(h, lib.rsfd_transmission(h, pg, pl, pr, K, T.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return T
+
+
+def rsfd_lead_sigma_uniform(Nx, Ny, h, fd_order, energies, eta):
+    """Host helper: returns (Sigma_L, Sigma_R) as complex128 arrays [K][ns][ns] in the ABI's
+    column-major layout (element (k, a, c) at [k, c, a]); Sigma is complex symmetric."""
+    lib = load_library()
+    e, ep = _f64(energies)
+    ns = (fd_order // 2) * Nx * Ny
+    SL = np.zeros((e.size, ns, ns), np.complex128)
+    SR = np.zeros((e.size, ns, ns), np.complex128)
+    st = lib.rsfd_lead_sigma_uniform(int(Nx), int(Ny), float(h), int(fd_order), ep, float(eta), int(e.size),
+                                     SL.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     SR.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(None, st)
+    return SL, SR
+
+
+def rsfd_destroy(h):
+    if h is not None and h.value:
+        load_library().rsfd_destroy(h)
+
+
+class Handle:
+    """Owns one rsfd handle; ``with Handle(...) as h:`` destroys it on exit."""
+
+    def __init__(self, grid, h, fd_order, V_loc, n_face=0, proj=None, precision=RSFD_FP64, stream=None):
+        self.grid, self.h, self.fd_order = tuple(grid), float(h), int(fd_order)
+        self.precision = precision
+        self.ptr = rsfd_create(grid, h, fd_order, V_loc, n_face, proj, precision, stream)
+        self.rows = rsfd_boundary_rows(self.ptr)
+        self.nb = int(self.rows.size)
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == RSFD_FP64 else torch.complex64
+
+    def close(self):
+        rsfd_destroy(self.ptr)
+        self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,383 @@
+// Dyson / OBM boundary step and Fisher-Lee transmission.
+//
+// G0_bb -> G_bb: the exact relation of Eq. sec3-01a restricted to the boundary rows is the
+// linear system (I - G0_bb Sigma_bb) G_bb = G0_bb with Sigma_bb = diag(Sigma_L, Sigma_R)
+// (equivalent to the block formulas Eqs. sec3-02 ... sec3-06).  Every energy is an independent
+// dense complex solve of size nb; the batch is processed with:
+//   1. M = I - G0 Sigma           (batched complex GEMM, FP64)
+//   2. M = P L U                  (batched right-looking LU with partial pivoting, FP64)
+//   3. G = U^{-1} L^{-1} P G0     (batched triangular solves)
+//   4. FP64 iterative refinement: R = G0 - M G, G += M^{-1} R (twice), reporting ||R||/||G0||.
+// T(E) = Tr[Gamma_L G_RL^H Gamma_R G_RL] (Eq. TF) with Gamma = i (Sigma - Sigma^H) is two
+// GEMMs and a trace per energy.  All matrices are column-major per energy.
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <string>
+#include <vector>
+
+#include "rsfd_internal.cuh"
+
+namespace rsfd {
+namespace {
+
+constexpr int GT = 16;   // GEMM tile
+
+// C[b] = alpha * op(A[b]) * B[b] + beta * C[b];  op = N or H (conjugate transpose).
+// A: if opA == 0, m x k (lda); if opA == 1, k x m stored, used as its conjugate transpose.
+__global__ void zgemm_batched(int m, int n, int k, double2 alpha, const double2* A, int lda, long long sA, int opA,
+                              const double2* B, int ldb, long long sB, double2 beta, double2* C, int ldc,
+                              long long sC) {
+  __shared__ double2 As[GT][GT + 1];
+  __shared__ double2 Bs[GT][GT + 1];
+  const int bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int row = blockIdx.y * GT + ty;   // i in C
+  const int col = blockIdx.x * GT + tx;   // j in C
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < k; k0 += GT) {
+    // A tile: rows blockIdx.y*GT + ty, cols k0 + tx
+    {
+      const int i = blockIdx.y * GT + ty, kk = k0 + tx;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < m && kk < k) {
+        if (opA == 0) v = A[(long long)kk * lda + i];
+        else {
+          v = A[(long long)i * lda + kk];
+          v.y = -v.y;
+        }
+      }
+      As[ty][tx] = v;
+    }
+    {
+      const int kk = k0 + ty, j = blockIdx.x * GT + tx;
+      Bs[ty][tx] = (kk < k && j < n) ? B[(long long)j * ldb + kk] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < GT; ++t) {
+      const double2 a = As[ty][t], b = Bs[t][tx];
+      acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+      acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+    }
+    __syncthreads();
+  }
+  if (row < m && col < n) {
+    double2* c = C + (long long)col * ldc + row;
+    double2 old = (beta.x != 0.0 || beta.y != 0.0) ? *c : make_double2(0.0, 0.0);
+    *c = cadd(cmul(alpha, acc), cmul(beta, old));
+  }
+}
+
+void zgemm(cudaStream_t st, int batch, int m, int n, int k, double2 alpha, const double2* A, int lda, long long sA,
+           int opA, const double2* B, int ldb, long long sB, double2 beta, double2* C, int ldc, long long sC) {
+  dim3 grid((n + GT - 1) / GT, (m + GT - 1) / GT, batch), block(GT, GT);
+  zgemm_batched<<<grid, block, 0, st>>>(m, n, k, alpha, A, lda, sA, opA, B, ldb, sB, beta, C, ldc, sC);
+}
+
+template <typename T>
+__global__ void to_c128(const T* src, double2* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = make_double2((double)src[i].x, (double)src[i].y);
+}
+__global__ void from_c128_f(const double2* src, float2* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+__global__ void copy_c128(const double2* src, double2* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// M = I - G0 * blockdiag(SL, SR) is formed by two GEMMs after M = I.
+__global__ void set_identity(double2* M, int nb, int batch) {
+  const long long n2 = (long long)nb * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2 * batch;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t % n2;
+    const long long c = e / nb, r = e - c * nb;
+    M[t] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// In-place LU with partial pivoting of one nb x nb matrix per CTA (right-looking, unblocked).
+__global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* piv, int* info) {
+  const int b = blockIdx.x;
+  double2* A = M + (long long)b * nb * nb;
+  int* pv = piv + (long long)b * nb;
+  __shared__ double s_val[256];
+  __shared__ int s_idx[256];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int j = 0; j < nb; ++j) {
+    // pivot search in column j
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + tid; i < nb; i += nt) {
+      const double v = cabs2(A[(long long)j * nb + i]);
+      if (v > best) { best = v; bi = i; }
+    }
+    s_val[tid] = best;
+    s_idx[tid] = bi;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        if (s_val[tid + s] > s_val[tid] || (s_val[tid + s] == s_val[tid] && s_idx[tid + s] < s_idx[tid])) {
+          s_val[tid] = s_val[tid + s];
+          s_idx[tid] = s_idx[tid + s];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      s_p = s_idx[0];
+      pv[j] = s_p;
+      if (!(s_val[0] > 0.0)) info[b] = j + 1;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      for (int c = tid; c < nb; c += nt) {
+        const double2 t = A[(long long)c * nb + j];
+        A[(long long)c * nb + j] = A[(long long)c * nb + p];
+        A[(long long)c * nb + p] = t;
+      }
+    }
+    __syncthreads();
+    const double2 d = A[(long long)j * nb + j];
+    const double2 inv = (d.x != 0.0 || d.y != 0.0) ? cdiv(make_double2(1.0, 0.0), d) : make_double2(0.0, 0.0);
+    for (int i = j + 1 + tid; i < nb; i += nt) A[(long long)j * nb + i] = cmul(A[(long long)j * nb + i], inv);
+    __syncthreads();
+    const int rem = nb - j - 1;
+    const long long tot = (long long)rem * rem;
+    for (long long t = tid; t < tot; t += nt) {
+      const int c = j + 1 + (int)(t / rem), i = j + 1 + (int)(t % rem);
+      const double2 l = A[(long long)j * nb + i], u = A[(long long)c * nb + j];
+      double2& a = A[(long long)c * nb + i];
+      a = csub(a, cmul(l, u));
+    }
+    __syncthreads();
+  }
+}
+
+// Solve (P L U) X = B in place for nrhs columns; one thread per right-hand side column.
+__global__ void zgetrs_batched(const double2* LU, const int* piv, double2* B, int nb, int nrhs) {
+  const int b = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nrhs) return;
+  const double2* A = LU + (long long)b * nb * nb;
+  const int* pv = piv + (long long)b * nb;
+  double2* x = B + ((long long)b * nrhs + c) * nb;
+  for (int j = 0; j < nb; ++j) {
+    const int p = pv[j];
+    if (p != j) {
+      const double2 t = x[j];
+      x[j] = x[p];
+      x[p] = t;
+    }
+  }
+  for (int i = 0; i < nb; ++i) {       // unit lower
+    double2 s = x[i];
+    for (int k = 0; k < i; ++k) s = csub(s, cmul(A[(long long)k * nb + i], x[k]));
+    x[i] = s;
+  }
+  for (int i = nb - 1; i >= 0; --i) {  // upper
+    double2 s = x[i];
+    for (int k = i + 1; k < nb; ++k) s = csub(s, cmul(A[(long long)k * nb + i], x[k]));
+    x[i] = cdiv(s, A[(long long)i * nb + i]);
+  }
+}
+
+__global__ void axpy_c128(double2* y, const double2* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = cadd(y[i], x[i]);
+}
+
+// out[b] = sum |A[b]|^2 over n2 entries (FP64, block per batch entry)
+__global__ void frob2_batched(const double2* A, long long n2, double* out) {
+  const int b = blockIdx.x;
+  const double2* a = A + (long long)b * n2;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n2; i += blockDim.x) s += cabs2(a[i]);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = red[0];
+}
+
+// Gamma = i (S - S^H) for a batch of ns x ns matrices
+__global__ void gamma_batched(const double2* S, double2* G, int ns, int batch) {
+  const long long n2 = (long long)ns * ns;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2 * batch;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n2, e = t - b * n2;
+    const int c = (int)(e / ns), r = (int)(e - (long long)c * ns);
+    const double2 a = S[t], bt = S[b * n2 + (long long)r * ns + c];   // S[c, r]
+    // S - S^H at (r, c) = a - conj(S[c, r]);  times i
+    const double2 d = make_double2(a.x - bt.x, a.y + bt.y);
+    G[t] = make_double2(-d.y, d.x);
+  }
+}
+
+// T[b] = Re sum_{a,c} GL[a,c] * W[c,a]
+__global__ void trace_prod_batched(const double2* GL, const double2* W, int ns, double* T, double* Ti) {
+  const int b = blockIdx.x;
+  const long long n2 = (long long)ns * ns;
+  const double2* g = GL + (long long)b * n2;
+  const double2* w = W + (long long)b * n2;
+  double sr = 0.0, si = 0.0;
+  for (long long t = threadIdx.x; t < n2; t += blockDim.x) {
+    const int c = (int)(t / ns), a = (int)(t - (long long)c * ns);
+    const double2 x = g[t], y = w[(long long)a * ns + c];   // GL[a,c], W[c,a]
+    sr += x.x * y.x - x.y * y.y;
+    si += x.x * y.y + x.y * y.x;
+  }
+  __shared__ double r1[256], r2[256];
+  r1[threadIdx.x] = sr;
+  r2[threadIdx.x] = si;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      r1[threadIdx.x] += r1[threadIdx.x + k];
+      r2[threadIdx.x] += r2[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    T[b] = r1[0];
+    Ti[b] = r2[0];
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
+}
+
+}  // namespace
+
+#define DY_CK(h, call)                                                                                  \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return handle_fail((h), RSFD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres) {
+  const int nb = handle_nb(h);
+  const int ns = nb / 2;
+  const long long n2 = (long long)nb * nb;
+  const bool fp64 = handle_prec(h) == RSFD_FP64;
+  rsfd_status s;
+  void *pG0, *pM, *pLU, *pX, *pR, *pPiv, *pRed;
+  if ((s = handle_ensure(h, 0, n2 * K * sizeof(double2), &pG0)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 1, n2 * K * sizeof(double2), &pM)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, n2 * K * sizeof(double2), &pLU)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 3, n2 * K * sizeof(double2), &pX)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, n2 * K * sizeof(double2), &pR)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 5, (long long)K * (nb + 1) * sizeof(int), &pPiv)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pRed)) != RSFD_OK) return s;
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = handle_stream(h);
+  double2* dG0 = (double2*)pG0;
+  double2* dM = (double2*)pM;
+  double2* dLU = (double2*)pLU;
+  double2* dX = (double2*)pX;
+  double2* dR = (double2*)pR;
+  int* piv = (int*)pPiv;
+  int* info = piv + (long long)K * nb;
+  double* red = (double*)pRed;
+  const long long tot = n2 * K;
+  if (fp64) copy_c128<<<grid_for(tot), 256, 0, st>>>((const double2*)G0, dG0, tot);
+  else to_c128<float2><<<grid_for(tot), 256, 0, st>>>((const float2*)G0, dG0, tot);
+  set_identity<<<grid_for(tot), 256, 0, st>>>(dM, nb, K);
+  const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  // M[:, :ns] -= G0[:, :ns] SL ;  M[:, ns:] -= G0[:, ns:] SR
+  zgemm(st, K, nb, ns, ns, m1, dG0, nb, n2, 0, (const double2*)SL, ns, (long long)ns * ns, one, dM, nb, n2);
+  zgemm(st, K, nb, ns, ns, m1, dG0 + (long long)ns * nb, nb, n2, 0, (const double2*)SR, ns, (long long)ns * ns, one,
+        dM + (long long)ns * nb, nb, n2);
+  copy_c128<<<grid_for(tot), 256, 0, st>>>(dM, dLU, tot);
+  DY_CK(h, cudaMemsetAsync(info, 0, K * sizeof(int), st));
+  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dX, tot);
+  {
+    dim3 g((nb + 127) / 128, K);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dX, nb, nb);
+  }
+  // iterative refinement in FP64
+  for (int it = 0; it < 2; ++it) {
+    copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dR, tot);
+    zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+    dim3 g((nb + 127) / 128, K);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dR, nb, nb);
+    axpy_c128<<<grid_for(tot), 256, 0, st>>>(dX, dR, tot);
+  }
+  if (refres) {
+    copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dR, tot);
+    zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+    frob2_batched<<<K, 256, 0, st>>>(dR, n2, red);
+    frob2_batched<<<K, 256, 0, st>>>(dG0, n2, red + K);
+  }
+  if (fp64) copy_c128<<<grid_for(tot), 256, 0, st>>>(dX, (double2*)G, tot);
+  else from_c128_f<<<grid_for(tot), 256, 0, st>>>(dX, (float2*)G, tot);
+  DY_CK(h, cudaGetLastError());
+  std::vector<int> hinfo(K);
+  DY_CK(h, cudaMemcpyAsync(hinfo.data(), info, K * sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hred(2 * K);
+  if (refres) DY_CK(h, cudaMemcpyAsync(hred.data(), red, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DY_CK(h, cudaStreamSynchronize(st));
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  if (refres)
+    for (int k = 0; k < K; ++k) refres[k] = sqrt(hred[k]) / sqrt(hred[K + k] > 0 ? hred[K + k] : 1.0);
+  for (int k = 0; k < K; ++k)
+    if (hinfo[k] != 0)
+      return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_dyson_boundary: singular I - G0 Sigma at energy " + std::to_string(k));
+  (void)zero;
+  return RSFD_OK;
+}
+
+rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const void* SR, int K, double* T) {
+  const int nb = handle_nb(h);
+  const int ns = nb / 2;
+  const long long n2 = (long long)nb * nb, s2 = (long long)ns * ns;
+  const bool fp64 = handle_prec(h) == RSFD_FP64;
+  rsfd_status s;
+  void *pG, *pGL, *pGR, *pW1, *pW2, *pT;
+  if ((s = handle_ensure(h, 0, n2 * K * sizeof(double2), &pG)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 1, s2 * K * sizeof(double2), &pGL)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, s2 * K * sizeof(double2), &pGR)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 3, s2 * K * sizeof(double2), &pW1)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, s2 * K * sizeof(double2), &pW2)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pT)) != RSFD_OK) return s;
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = handle_stream(h);
+  double2* dG = (double2*)pG;
+  const long long tot = n2 * K;
+  if (fp64) copy_c128<<<grid_for(tot), 256, 0, st>>>((const double2*)G, dG, tot);
+  else to_c128<float2><<<grid_for(tot), 256, 0, st>>>((const float2*)G, dG, tot);
+  gamma_batched<<<grid_for(s2 * K), 256, 0, st>>>((const double2*)SL, (double2*)pGL, ns, K);
+  gamma_batched<<<grid_for(s2 * K), 256, 0, st>>>((const double2*)SR, (double2*)pGR, ns, K);
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  const double2* GRL = dG + ns;   // rows ns.., cols 0..ns-1, leading dimension nb
+  // W1 = Gamma_R G_RL ; W2 = G_RL^H W1
+  zgemm(st, K, ns, ns, ns, one, (const double2*)pGR, ns, s2, 0, GRL, nb, n2, zero, (double2*)pW1, ns, s2);
+  zgemm(st, K, ns, ns, ns, one, GRL, nb, n2, 1, (const double2*)pW1, ns, s2, zero, (double2*)pW2, ns, s2);
+  double* dT = (double*)pT;
+  trace_prod_batched<<<K, 256, 0, st>>>((const double2*)pGL, (const double2*)pW2, ns, dT, dT + K);
+  DY_CK(h, cudaGetLastError());
+  std::vector<double> hT(2 * K);
+  DY_CK(h, cudaMemcpyAsync(hT.data(), dT, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DY_CK(h, cudaStreamSynchronize(st));
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  for (int k = 0; k < K; ++k) T[k] = hT[k];
+  return RSFD_OK;
+}
+
+}  // namespace rsfd

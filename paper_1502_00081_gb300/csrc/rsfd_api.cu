@@ -1,0 +1,541 @@
+// C ABI entry points, the handle, and the host-side column scheduler of the shifted COCG solve.
+//
+// The scheduler keeps W right-hand sides ("slots") in flight.  Each device iteration is one
+// fused pass (seed SpMV + seed update + dots + FP64 scalar step) and one shift update over all
+// slots; a chunk of iterations is captured once in a CUDA graph and replayed.  Between replays
+// the host reads the slot states (a few hundred bytes), records the columns that finished and
+// loads new columns into the freed slots, so slots never wait for the slowest column of a block.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "rsfd_internal.cuh"
+
+namespace rsfd {
+
+static thread_local std::string g_last_error = "no error";
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Handle {
+  int nx = 0, ny = 0, nz = 0;
+  long long N = 0;
+  double h = 0;
+  int fd_order = 2, R = 1, nface = 1, nb = 0;
+  int prec = RSFD_FP64;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int device = 0;
+  std::vector<int64_t> brow;
+  void* dV = nullptr;
+  int64_t* dbrow = nullptr;
+  // nonlocal projectors (host copy; the device path for them is not built yet)
+  int n_atoms = 0;
+  rsfd_solve_opts opts;
+  rsfd_stats stats;
+  std::string err = "no error";
+  // solver workspace
+  DevBuf rbuf, pbuf, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
+  // dyson / transmission workspace
+  DevBuf dy[8];
+};
+
+rsfd_status fail(Handle* h, rsfd_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+#define RSFD_CK(h, call)                                                                              \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      return fail((h), RSFD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    }                                                                                                 \
+  } while (0)
+
+static rsfd_status ensure(Handle* h, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return RSFD_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RSFD_ERR_ALLOC, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return RSFD_OK;
+}
+
+rsfd_status handle_ensure(Handle* h, int idx, size_t bytes, void** out) {
+  rsfd_status s = ensure(h, h->dy[idx], bytes);
+  if (s != RSFD_OK) return s;
+  *out = h->dy[idx].p;
+  return RSFD_OK;
+}
+
+cudaStream_t handle_stream(Handle* h) { return h->work; }
+int handle_prec(Handle* h) { return h->prec; }
+int handle_nb(Handle* h) { return h->nb; }
+rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& m) { return fail(h, s, m); }
+
+// order the internal stream after the caller's stream
+rsfd_status handle_begin(Handle* h) {
+  RSFD_CK(h, cudaSetDevice(h->device));
+  RSFD_CK(h, cudaEventRecord(h->ev_in, h->user_stream));
+  RSFD_CK(h, cudaStreamWaitEvent(h->work, h->ev_in, 0));
+  return RSFD_OK;
+}
+// order the caller's stream after the internal stream
+rsfd_status handle_end(Handle* h) {
+  RSFD_CK(h, cudaEventRecord(h->ev_out, h->work));
+  RSFD_CK(h, cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+  return RSFD_OK;
+}
+
+static void free_all(Handle* h) {
+  DevBuf* bufs[] = {&h->rbuf, &h->pbuf, &h->slots, &h->shifts, &h->partials, &h->tickets,
+                    &h->Z, &h->init_list, &h->init_grid, &h->counters};
+  for (DevBuf* b : bufs) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+  for (auto& b : h->dy) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  if (h->dV) cudaFree(h->dV);
+  if (h->dbrow) cudaFree(h->dbrow);
+  h->dV = nullptr;
+  h->dbrow = nullptr;
+}
+
+static StencilCoef stencil_coef(int fd_order, double hh) {
+  // -1/2 d^2/dx^2 with central coefficients (1,-2,1)/h^2 or (-1/12,4/3,-5/2,4/3,-1/12)/h^2 per axis
+  StencilCoef c;
+  const double ih2 = 1.0 / (hh * hh);
+  if (fd_order == 2) {
+    c.hd = 3.0 * (-0.5 * -2.0) * ih2;
+    c.hk[0] = -0.5 * 1.0 * ih2;
+    c.hk[1] = 0.0;
+  } else {
+    c.hd = 3.0 * (-0.5 * -2.5) * ih2;
+    c.hk[0] = -0.5 * (4.0 / 3.0) * ih2;
+    c.hk[1] = -0.5 * (-1.0 / 12.0) * ih2;
+  }
+  c.hk[2] = 0.0;
+  return c;
+}
+
+}  // namespace rsfd
+
+using namespace rsfd;
+
+struct rsfd_handle_s : public rsfd::Handle {};
+
+extern "C" {
+
+rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int32_t fd_order, int32_t n_face,
+                        const double* V_loc, const rsfd_projectors* proj, int32_t precision, void* stream) {
+  if (!out) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: out is NULL");
+  *out = nullptr;
+  if (!grid || !V_loc) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: grid and V_loc must be non-NULL");
+  if (grid[0] < 1 || grid[1] < 1 || grid[2] < 2) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: grid sizes must be >= 1 (Nz >= 2)");
+  if (!(hh > 0) || !isfinite(hh)) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: h must be positive");
+  if (fd_order != 2 && fd_order != 4) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: fd_order must be 2 or 4");
+  if (precision != RSFD_FP64 && precision != RSFD_MIXED) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: bad precision");
+  const int R = fd_order / 2;
+  if (n_face == 0) n_face = R;
+  if (n_face < 1 || 2 * n_face > grid[2]) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: n_face must satisfy 1 <= n_face <= Nz/2");
+  const long long N = (long long)grid[0] * grid[1] * grid[2];
+  if (N > (1ll << 31) - 1) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: grid too large (N >= 2^31)");
+  if (proj && proj->n_atoms > 0) {
+    return fail(nullptr, RSFD_ERR_UNSUPPORTED, "rsfd_create: nonlocal projectors are not supported by this build");
+  }
+  for (long long i = 0; i < N; ++i) {
+    if (!isfinite(V_loc[i])) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: V_loc has a non-finite entry");
+  }
+  rsfd_handle_s* h = new (std::nothrow) rsfd_handle_s();
+  if (!h) return fail(nullptr, RSFD_ERR_ALLOC, "rsfd_create: host allocation failed");
+  h->nx = grid[0];
+  h->ny = grid[1];
+  h->nz = grid[2];
+  h->N = N;
+  h->h = hh;
+  h->fd_order = fd_order;
+  h->R = R;
+  h->nface = n_face;
+  h->prec = precision;
+  h->user_stream = reinterpret_cast<cudaStream_t>(stream);
+  memset(&h->opts, 0, sizeof(h->opts));
+  memset(&h->stats, 0, sizeof(h->stats));
+  const long long nxy = (long long)h->nx * h->ny;
+  h->nb = (int)(2 * n_face * nxy);
+  h->brow.resize(h->nb);
+  for (int pl = 0; pl < 2 * n_face; ++pl) {
+    const long long z = pl < n_face ? pl : (h->nz - 2 * n_face + pl);
+    for (long long o = 0; o < nxy; ++o) h->brow[pl * nxy + o] = z * nxy + o;
+  }
+  auto bail = [&](rsfd_status s, const std::string& m) {
+    free_all(h);
+    if (h->work) cudaStreamDestroy(h->work);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    delete h;
+    return fail(nullptr, s, m);
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = kernels_init();
+  if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  const size_t vsz = precision == RSFD_FP64 ? sizeof(double) : sizeof(float);
+  e = cudaMalloc(&h->dV, N * vsz);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->dbrow, h->nb * sizeof(int64_t));
+  if (e != cudaSuccess) return bail(RSFD_ERR_ALLOC, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  if (precision == RSFD_FP64) {
+    e = cudaMemcpy(h->dV, V_loc, N * sizeof(double), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> vf(N);
+    for (long long i = 0; i < N; ++i) vf[i] = (float)V_loc[i];
+    e = cudaMemcpy(h->dV, vf.data(), N * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h->dbrow, h->brow.data(), h->nb * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  *out = h;
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows) {
+  if (!h || !nb) return fail(h, RSFD_ERR_ARG, "rsfd_boundary_rows: NULL argument");
+  *nb = h->nb;
+  if (rows) memcpy(rows, h->brow.data(), h->nb * sizeof(int64_t));
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
+  if (!h) return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: NULL handle");
+  if (!o) {
+    memset(&h->opts, 0, sizeof(h->opts));
+    return RSFD_OK;
+  }
+  if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
+  if (o->tile_y > 0 && (pass_threads(h->R, o->tile_y) > 640 || pass_threads(h->R, o->tile_y) % 32 != 0))
+    return fail(h, RSFD_ERR_ARG,
+                "rsfd_set_solve_options: tile_y must give (32+4R)*(tile_y+4R) <= 640 threads, a multiple of 32");
+  h->opts = *o;
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out) {
+  if (!h || !out) return fail(h, RSFD_ERR_ARG, "rsfd_get_stats: NULL argument");
+  *out = h->stats;
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+                              double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
+                              void* G0_bb, rsfd_col_info* info, double* final_res) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg: NULL handle");
+  if (!cols || ncols < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: need ncols >= 1 columns");
+  if (!energies || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: need K >= 1 energies");
+  if (!(eta > 0) || !isfinite(eta)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: eta must be positive");
+  if (!(tol > 0) || !(tol < 1)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: tol must lie in (0, 1)");
+  if (maxit < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: maxit must be >= 1");
+  if (!G0_bb) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: G0_bb is NULL");
+  for (int k = 0; k < K; ++k)
+    if (!isfinite(energies[k])) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: non-finite energy");
+  for (int c = 0; c < ncols; ++c)
+    if (cols[c] < 0 || cols[c] >= h->N) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: column index out of range");
+  int seed0 = 0;
+  if (seed_kind == RSFD_SEED_MID) seed0 = K / 2;
+  else if (seed_kind == RSFD_SEED_FIRST) seed0 = 0;
+  else if (seed_kind == RSFD_SEED_INDEX) {
+    if (seed_index < 0 || seed_index >= K) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: seed_index out of range");
+    seed0 = seed_index;
+  } else {
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: bad seed_kind");
+  }
+  const bool fp64 = h->prec == RSFD_FP64;
+  const size_t vsz = fp64 ? 16 : 8;
+
+  // ---- launch shape
+  SolveDims d;
+  memset(&d, 0, sizeof(d));
+  d.nx = h->nx;
+  d.ny = h->ny;
+  d.nz = h->nz;
+  d.N = h->N;
+  d.R = h->R;
+  d.nface = h->nface;
+  d.nb = h->nb;
+  d.K = K;
+  d.ncols = ncols;
+  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : (h->R == 2 ? 8 : 12);
+  if (pass_threads(h->R, d.tile_y) > 640 || pass_threads(h->R, d.tile_y) % 32 != 0)
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y for this stencil order");
+  d.zchunk = h->opts.z_chunk > 0 ? h->opts.z_chunk : std::min(h->nz, 32);
+  d.tiles_x = (h->nx + pass_tile_x(h->R) - 1) / pass_tile_x(h->R);
+  d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
+  d.nzchunks = (h->nz + d.zchunk - 1) / d.zchunk;
+  d.ctas_per_slot = d.tiles_x * d.tiles_y * d.nzchunks;
+  int W = h->opts.slots > 0 ? h->opts.slots : 64;
+  W = std::min(W, ncols);
+  {
+    size_t freeb = 0, totb = 0;
+    RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));
+    const size_t per_slot = 3 * (size_t)h->N * vsz + (size_t)K * h->nb * vsz + (size_t)K * sizeof(ShiftState) +
+                            (size_t)d.ctas_per_slot * 64 + 256;
+    const size_t have = h->rbuf.bytes + h->pbuf.bytes;
+    const size_t budget = (size_t)(0.6 * (double)(freeb + have));
+    if (h->opts.slots <= 0) {
+      while (W > 1 && per_slot * W > budget) W /= 2;
+    }
+  }
+  d.W = W;
+  const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
+  const bool use_graphs = h->opts.use_graphs >= 0 && !h->opts.profile;
+
+  // ---- workspace
+  rsfd_status s;
+  if ((s = ensure(h, h->rbuf, (size_t)W * 3 * h->N * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->slots, (size_t)W * sizeof(SlotState))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->shifts, (size_t)W * K * sizeof(ShiftState))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->partials, (size_t)W * d.ctas_per_slot * 8 * sizeof(double))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->tickets, (size_t)W * sizeof(unsigned int))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->Z, (size_t)K * sizeof(double2))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->init_list, (size_t)W * 2 * sizeof(int))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->init_grid, (size_t)W * sizeof(long long))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->counters, 4 * sizeof(unsigned long long))) != RSFD_OK) return s;
+  SolverBuffers b;
+  b.rbuf = h->rbuf.p;
+  b.pbuf = h->pbuf.p;
+  b.V = h->dV;
+  b.slots = (SlotState*)h->slots.p;
+  b.shifts = (ShiftState*)h->shifts.p;
+  b.partials = (double*)h->partials.p;
+  b.tickets = (unsigned int*)h->tickets.p;
+  b.Z = (double2*)h->Z.p;
+  b.brow = h->dbrow;
+  b.G0 = G0_bb;
+  b.init_list = (int*)h->init_list.p;
+  b.init_grid = (long long*)h->init_grid.p;
+  b.counters = (unsigned long long*)h->counters.p;
+  const StencilCoef coef = stencil_coef(h->fd_order, h->h);
+
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = h->work;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  RSFD_CK(h, cudaEventCreate(&t0));
+  RSFD_CK(h, cudaEventCreate(&t1));
+  RSFD_CK(h, cudaEventRecord(t0, st));
+
+  std::vector<double2> Zh(K);
+  for (int k = 0; k < K; ++k) Zh[k] = make_double2(energies[k], eta);
+  RSFD_CK(h, cudaMemcpyAsync(b.Z, Zh.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
+  RSFD_CK(h, cudaMemsetAsync(b.tickets, 0, W * sizeof(unsigned int), st));
+  RSFD_CK(h, cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned long long), st));
+  std::vector<SlotState> hs(W);
+  for (int w = 0; w < W; ++w) {
+    memset(&hs[w], 0, sizeof(SlotState));
+    hs[w].col = -1;
+    hs[w].status = SLOT_EMPTY;
+    hs[w].k4_n = -1;
+  }
+  RSFD_CK(h, cudaMemcpyAsync(b.slots, hs.data(), W * sizeof(SlotState), cudaMemcpyHostToDevice, st));
+
+  memset(&h->stats, 0, sizeof(h->stats));
+  h->stats.slots = W;
+  h->stats.iters_per_sync = C;
+  std::vector<int> slot_col(W, -1);
+  std::vector<int> init_list(2 * W);
+  std::vector<long long> init_grid(W);
+  std::vector<ShiftState> hsh(K);
+  int next = 0;
+  rsfd_status worst = RSFD_OK;
+
+  auto assign = [&](std::vector<int>& free_slots) -> rsfd_status {
+    int n_init = 0;
+    for (int w : free_slots) {
+      if (next >= ncols) break;
+      init_list[2 * n_init] = w;
+      init_list[2 * n_init + 1] = next;
+      init_grid[n_init] = cols[next];
+      slot_col[w] = next;
+      ++next;
+      ++n_init;
+    }
+    if (n_init == 0) return RSFD_OK;
+    RSFD_CK(h, cudaMemcpyAsync(b.init_list, init_list.data(), 2 * n_init * sizeof(int), cudaMemcpyHostToDevice, st));
+    RSFD_CK(h, cudaMemcpyAsync(b.init_grid, init_grid.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, st));
+    RSFD_CK(h, launch_slot_init(fp64, d, b, n_init, seed0, st));
+    // the host arrays are reused: wait until the copies have been consumed
+    RSFD_CK(h, cudaStreamSynchronize(st));
+    h->stats.n_other += 1;
+    return RSFD_OK;
+  };
+
+  {
+    std::vector<int> all(W);
+    for (int w = 0; w < W; ++w) all[w] = w;
+    if ((s = assign(all)) != RSFD_OK) return s;
+  }
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<cudaEvent_t> pev;
+  if (h->opts.profile) {
+    pev.resize(4 * C);
+    for (auto& e : pev) RSFD_CK(h, cudaEventCreate(&e));
+  }
+  auto issue_chunk = [&]() -> rsfd_status {
+    for (int t = 0; t < C; ++t) {
+      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 0], st));
+      RSFD_CK(h, launch_pass(fp64, d, b, coef, tol, maxit, st));
+      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 1], st));
+      RSFD_CK(h, launch_shift(fp64, d, b, st));
+      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 2], st));
+    }
+    return RSFD_OK;
+  };
+  if (use_graphs) {
+    RSFD_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    rsfd_status cs = issue_chunk();
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (cs != RSFD_OK) return cs;
+    RSFD_CK(h, ce);
+    RSFD_CK(h, cudaGraphInstantiate(&gexec, graph, 0));
+  }
+
+  int64_t iter_sum = 0;
+  for (;;) {
+    if (use_graphs) {
+      RSFD_CK(h, cudaGraphLaunch(gexec, st));
+    } else {
+      if ((s = issue_chunk()) != RSFD_OK) return s;
+    }
+    h->stats.n_pass += C;
+    h->stats.n_shift += C;
+    RSFD_CK(h, cudaMemcpyAsync(hs.data(), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
+    RSFD_CK(h, cudaStreamSynchronize(st));
+    if (h->opts.profile) {
+      for (int t = 0; t < C; ++t) {
+        float a = 0, c2 = 0;
+        RSFD_CK(h, cudaEventElapsedTime(&a, pev[4 * t + 0], pev[4 * t + 1]));
+        RSFD_CK(h, cudaEventElapsedTime(&c2, pev[4 * t + 1], pev[4 * t + 2]));
+        h->stats.ms_pass += a;
+        h->stats.ms_shift += c2;
+      }
+    }
+    std::vector<int> freed;
+    for (int w = 0; w < W; ++w) {
+      if (slot_col[w] < 0) continue;
+      if (hs[w].status == SLOT_RUNNING) continue;
+      const int c = slot_col[w];
+      rsfd_status cs = RSFD_OK;
+      if (hs[w].status == SLOT_MAXIT) cs = RSFD_ERR_NOT_CONVERGED;
+      if (hs[w].status == SLOT_BREAKDOWN) cs = RSFD_ERR_BREAKDOWN;
+      if (cs != RSFD_OK && (worst == RSFD_OK || cs == RSFD_ERR_BREAKDOWN)) worst = cs;
+      iter_sum += hs[w].iters;
+      if (info) {
+        info[c].iters = hs[w].iters;
+        info[c].switches = hs[w].switches;
+        info[c].status = cs;
+        info[c].final_seed = hs[w].seed;
+      }
+      if (final_res) {
+        RSFD_CK(h, cudaMemcpy(hsh.data(), b.shifts + (size_t)w * K, K * sizeof(ShiftState), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < K; ++k) final_res[(size_t)c * K + k] = hsh[k].res;
+      }
+      slot_col[w] = -1;
+      freed.push_back(w);
+    }
+    if (!freed.empty() && next < ncols) {
+      if ((s = assign(freed)) != RSFD_OK) return s;
+    }
+    bool any = false;
+    for (int w = 0; w < W; ++w) any |= slot_col[w] >= 0;
+    if (!any && next >= ncols) break;
+  }
+  RSFD_CK(h, cudaEventRecord(t1, st));
+  RSFD_CK(h, cudaEventSynchronize(t1));
+  float ms = 0;
+  RSFD_CK(h, cudaEventElapsedTime(&ms, t0, t1));
+  h->stats.ms_total = ms;
+  unsigned long long cnt[4];
+  RSFD_CK(h, cudaMemcpy(cnt, b.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  h->stats.shift_updates = (int64_t)cnt[0];
+  h->stats.slot_iterations = iter_sum;
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& e : pev) cudaEventDestroy(e);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  if (worst != RSFD_OK) {
+    h->err = worst == RSFD_ERR_BREAKDOWN ? "rsfd_shifted_cocg: breakdown in at least one column"
+                                         : "rsfd_shifted_cocg: at least one column reached maxit";
+  }
+  return worst;
+}
+
+rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+                                int32_t K, void* G_bb, double* refine_residual) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_boundary: NULL handle");
+  if (!G0_bb || !Sigma_L || !Sigma_R || !G_bb || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_boundary: bad arguments");
+  if (G0_bb == G_bb) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_boundary: G_bb may not alias G0_bb");
+  return dyson_run(h, G0_bb, Sigma_L, Sigma_R, K, G_bb, refine_residual);
+}
+
+rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                              double* T) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_transmission: NULL handle");
+  if (!G_bb || !Sigma_L || !Sigma_R || !T || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_transmission: bad arguments");
+  return transmission_run(h, G_bb, Sigma_L, Sigma_R, K, T);
+}
+
+rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double hh, int32_t fd_order, const double* energies,
+                                    double eta, int32_t K, double* Sigma_L, double* Sigma_R) {
+  if (Nx < 1 || Ny < 1 || !(hh > 0) || (fd_order != 2 && fd_order != 4) || !energies || K < 1 || !Sigma_L ||
+      !Sigma_R || !(eta > 0))
+    return fail(nullptr, RSFD_ERR_ARG, "rsfd_lead_sigma_uniform: bad arguments");
+  std::string err;
+  rsfd_status s = lead_sigma_uniform(Nx, Ny, hh, fd_order, energies, eta, K, Sigma_L, Sigma_R, &err);
+  if (s != RSFD_OK) return fail(nullptr, s, err);
+  return RSFD_OK;
+}
+
+const char* rsfd_last_error(rsfd_handle h) {
+  if (h) return h->err.c_str();
+  return g_last_error.c_str();
+}
+
+void rsfd_destroy(rsfd_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->work) cudaStreamSynchronize(h->work);
+  free_all(h);
+  if (h->work) cudaStreamDestroy(h->work);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  delete h;
+}
+
+}  // extern "C"

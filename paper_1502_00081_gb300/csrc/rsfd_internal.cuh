@@ -1,0 +1,156 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsfd.h"
+
+namespace rsfd {
+
+// ---------------------------------------------------------------------------------------------
+// complex helpers: float2 / double2 with interleaved (re, im)
+// ---------------------------------------------------------------------------------------------
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<double> { typedef double2 type; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  // Smith's algorithm for a / b
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// solver state in device memory
+// ---------------------------------------------------------------------------------------------
+enum SlotStatus : int32_t {
+  SLOT_EMPTY = -1,
+  SLOT_RUNNING = 0,
+  SLOT_DONE = 1,      // every energy converged
+  SLOT_MAXIT = 2,
+  SLOT_BREAKDOWN = 3,
+};
+
+// One in-flight right-hand side (a "slot").  Written by the scalar step of the pass kernel,
+// read by every CTA of the next pass and by the shift-update kernel.
+struct __align__(16) SlotState {
+  int32_t col;        // output column index c (G0_bb[:, :, c]); -1 when empty
+  int32_t n;          // index of the residual the next pass produces (r_n)
+  int32_t seed;       // current seed energy index s
+  int32_t status;     // SlotStatus
+  int32_t switches;   // seed switches so far
+  int32_t k4_n;       // iteration whose shift update is pending (-1 = none)
+  int32_t iters;      // seed iterations at exit
+  int32_t pad0;
+  double2 a1;         // next pass: r_n = a1 r_{n-1} + a2 r_{n-2} + aA (A r_{n-1})
+  double2 a2;
+  double2 aA;
+  double2 Zs;         // seed energy used by the next pass (A = Zs - H)
+  double2 alpha_prev; // alpha_{n-1}
+  double2 rr_prev;    // (r_{n-1}, r_{n-1}) in the current seed's normalisation
+};
+
+// Per (slot, energy) scalars (FP64).
+struct __align__(16) ShiftState {
+  double2 pi_n;       // pi_n^(s,i)
+  double2 pi_nm1;     // pi_{n-1}^(s,i)
+  double2 alpha_prev; // alpha_{n-1}^(i)
+  double2 cr;         // shift update coefficients of the pending iteration:
+  double2 cb;         //   p <- cr * r_n + cb * p ;  x <- x + ca * p
+  double2 ca;
+  double res;         // last residual ||r_n|| / |pi_n|
+  int32_t active;     // 1 while not converged
+  int32_t conv_iter;  // iteration at which it converged (-1 = not yet)
+};
+
+struct SolveDims {
+  int nx, ny, nz;
+  long long N;
+  int R;              // stencil reach (fd_order / 2)
+  int nface;          // boundary planes per side
+  int nb;             // boundary rows
+  int K;              // energies
+  int W;              // slots
+  int tile_y;         // stencil tile height (y); the tile width in x is fixed by the kernel
+  int tiles_x, tiles_y, zchunk, nzchunks, ctas_per_slot;
+  int ncols;
+};
+
+struct Handle;   // defined in rsfd_api.cu
+
+// Kernel launchers implemented in cocg_kernels.cu.
+struct SolverBuffers {
+  void* rbuf;             // [W][3][N] complex T
+  void* pbuf;             // [W][K][nb] complex T
+  void* V;                // [N] T
+  SlotState* slots;       // [W]
+  ShiftState* shifts;     // [W][K]
+  double* partials;       // [W][ctas_per_slot][8]
+  unsigned int* tickets;  // [W]
+  double2* Z;             // [K] complex energies
+  int64_t* brow;          // [nb] boundary rows
+  void* G0;               // output base
+  int* init_list;         // [W][2]: slot, column c
+  long long* init_grid;   // [W]: grid index j of the new column
+  unsigned long long* counters;  // [0] active (slot, energy) updates, [1] slot iterations
+};
+
+struct StencilCoef {
+  double hd;        // diagonal kinetic coefficient of H
+  double hk[3];     // H couplings to neighbours at distance 1..R along each axis
+};
+
+struct PassConfig {
+  int tile_x, tile_y;
+};
+
+// Launch one fused pass (stencil + seed update + dots + scalar step) over all slots.
+cudaError_t launch_pass(bool fp64, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
+                        int maxit, cudaStream_t st);
+// Launch the shift update of the pending iteration for all slots.
+cudaError_t launch_shift(bool fp64, const SolveDims& d, const SolverBuffers& b, cudaStream_t st);
+// Initialise n_init slots listed in b.init_list / b.init_grid.
+cudaError_t launch_slot_init(bool fp64, const SolveDims& d, const SolverBuffers& b, int n_init, int seed0,
+                             cudaStream_t st);
+int pass_tile_x(int R);
+cudaError_t kernels_init();
+// the pass kernel's warp-shuffle reductions need whole warps: (32 + 4R) * (tile_y + 4R) % 32 == 0
+int pass_threads(int R, int tile_y);
+
+// Handle services used by other translation units (rsfd_api.cu).
+rsfd_status handle_ensure(Handle* h, int idx, size_t bytes, void** out);   // workspace slot idx < 8
+cudaStream_t handle_stream(Handle* h);
+int handle_prec(Handle* h);
+int handle_nb(Handle* h);
+rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& msg);
+rsfd_status handle_begin(Handle* h);
+rsfd_status handle_end(Handle* h);
+
+// Dyson / transmission launchers (dyson.cu).
+rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres);
+rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const void* SR, int K, double* T);
+
+// Host lead self-energy (lead_sigma.cpp).
+rsfd_status lead_sigma_uniform(int nx, int ny, double h, int fd_order, const double* E, double eta, int K,
+                               double* SL, double* SR, std::string* err);
+
+}  // namespace rsfd

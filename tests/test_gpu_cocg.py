@@ -1,0 +1,138 @@
+"""GPU parity of the shifted COCG path (Sec. III B, Appendix) against the CPU oracle.
+
+All calls go through the C ABI (ctypes binding).  FP64 mode must match the oracle to a relative
+Frobenius error <= 1e-9; mixed mode (complex64 vectors, FP64 scalars and reductions) is compared
+with a bound derived from single precision (see the individual tests).
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import make_problem, small_problem          # noqa: E402
+from oracle.cocg import shifted_cocg_columns               # noqa: E402
+from oracle.operator import boundary_rows                  # noqa: E402
+from oracle.dense import g0_dense                          # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_00081_gb300.build_lib import build
+    build()
+    import paper_1502_00081_gb300 as m
+    m.load_library()
+    return m
+
+
+def gpu_g0(rs, p, precision, cols=None, opts=None, seed_kind=0, seed_index=0, tol=None, maxit=None):
+    cols = p.cols if cols is None else np.asarray(cols)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=precision) as h:
+        if opts:
+            rs.rsfd_set_solve_options(h.ptr, **opts)
+        G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, p.tol if tol is None else tol,
+                                             p.maxit if maxit is None else maxit, G0, seed_kind, seed_index)
+        stats = rs.rsfd_get_stats(h.ptr)
+        torch.cuda.synchronize()
+        out = G0.cpu().numpy().astype(np.complex128).transpose(0, 2, 1)   # [K, nb, ncols]
+    return st, out, info, res, stats
+
+
+def relf(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_tiny_wire_fp64_matches_oracle_and_dense(rs):
+    """The 8x8x12 2nd-order wire, all 128 plane columns, 8 energies, tol 1e-12."""
+    p = make_problem("tiny_wire_fp64")
+    st, G, info, res, stats = gpu_g0(rs, p, rs.RSFD_FP64)
+    assert st == rs.RSFD_OK
+    b = boundary_rows(p.grid, p.n_face)
+    Go, ores = shifted_cocg_columns(p)
+    assert relf(G, Go) <= 1e-9
+    for k in (0, 3, 7):
+        Gd = g0_dense(p, p.energies[k] + 1j * p.eta, rows=b, cols=p.cols)
+        assert relf(G[k], Gd) <= 1e-9
+    # complex symmetry of the boundary block (rows == cols here)
+    assert np.abs(G - G.transpose(0, 2, 1)).max() <= 1e-9 * np.abs(G).max()
+    assert (info["status"] == 0).all() and (res < p.tol).all()
+    # iteration counts agree with the oracle's to within a couple of steps (rounding order differs)
+    it_o = np.array([r.iterations for r in ores])
+    assert np.abs(info["iters"] - it_o).max() <= 3
+
+
+@pytest.mark.parametrize("grid,order,slots,tile_y,zc", [
+    ((37, 13, 45), 4, 3, 8, 16),     # ragged x, y and z tiles, slot refill
+    ((9, 33, 20), 2, 2, 12, 7),
+    ((5, 4, 6), 4, 8, 0, 0),         # tiles far larger than the grid
+])
+def test_ragged_tiles_fp64(rs, grid, order, slots, tile_y, zc):
+    p = small_problem(grid=grid, h=0.45, fd_order=order, n_wells=4, n_energies=5, e_range=(0.3, 2.5),
+                      eta=5e-2, tol=1e-12, cols=7)
+    st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_FP64, opts=dict(slots=slots, tile_y=tile_y, z_chunk=zc))
+    assert st == rs.RSFD_OK
+    Go, _ = shifted_cocg_columns(p)
+    assert relf(G, Go) <= 1e-9
+
+
+def test_seed_switching_and_policies(rs):
+    p = small_problem(grid=(7, 6, 12), h=0.5, fd_order=4, n_wells=3, n_energies=6, e_range=(-4.0, 3.0),
+                      eta=2e-2, tol=1e-12, cols=4)
+    Go, ores = shifted_cocg_columns(p, seed=0)
+    assert max(r.switches for r in ores) >= 1
+    for kind, idx in ((rs.RSFD_SEED_FIRST, 0), (rs.RSFD_SEED_MID, 0), (rs.RSFD_SEED_INDEX, 5)):
+        st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_FP64, seed_kind=kind, seed_index=idx)
+        assert st == rs.RSFD_OK
+        assert relf(G, Go) <= 1e-9
+        if kind == rs.RSFD_SEED_FIRST:
+            assert info["switches"].max() >= 1
+
+
+def test_launch_modes_bitwise_identical(rs):
+    """Graph replay, plain launches and profiled launches run the same fixed-order reductions."""
+    p = small_problem(grid=(16, 12, 20), h=0.45, fd_order=4, n_wells=3, n_energies=4, e_range=(0.2, 2.0),
+                      eta=3e-2, tol=1e-8, cols=6)
+    outs = []
+    for opts in (dict(slots=3), dict(slots=3, use_graphs=-1), dict(slots=3, profile=1), dict(slots=3, iters_per_sync=5)):
+        st, G, info, res, stats = gpu_g0(rs, p, rs.RSFD_MIXED, opts=opts)
+        assert st == rs.RSFD_OK
+        outs.append(G)
+        if opts.get("profile"):
+            assert stats["ms_pass"] > 0 and stats["ms_shift"] > 0
+    for G in outs[1:]:
+        assert np.array_equal(G, outs[0])
+
+
+def test_mixed_precision_matches_oracle(rs):
+    """complex64 Krylov vectors with FP64 scalars: error bounded by single-precision rounding
+    amplified by the conditioning; measured against the FP64 oracle."""
+    p = small_problem(grid=(24, 20, 32), h=0.4, fd_order=4, n_wells=6, n_energies=8, e_range=(-0.5, 0.5),
+                      eta=1e-2, tol=1e-7, cols=6)
+    st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_MIXED)
+    assert st == rs.RSFD_OK
+    Go, _ = shifted_cocg_columns(p, tol=1e-12)
+    err = relf(G, Go)
+    assert err <= 1e-5, err
+
+
+def test_maxit_reports_not_converged(rs):
+    p = small_problem(grid=(8, 8, 12), h=0.5, fd_order=2, n_wells=2, n_energies=3, eta=1e-3, tol=1e-12, cols=2)
+    st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_FP64, maxit=5)
+    assert st == rs.RSFD_ERR_NOT_CONVERGED
+    assert (info["iters"] == 5).all() and (info["status"] == rs.RSFD_ERR_NOT_CONVERGED).all()
+
+
+def test_argument_errors(rs):
+    p = small_problem(grid=(6, 5, 8), cols=2)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V) as h:
+        G0 = torch.zeros((p.K, 2, h.nb), dtype=torch.complex128, device="cuda")
+        for bad in (dict(cols=np.array([-1, 3])), dict(eta=0.0), dict(tol=2.0)):
+            args = dict(cols=p.cols, eta=p.eta, tol=p.tol)
+            args.update(bad)
+            with pytest.raises(rs.RsfdError):
+                rs.rsfd_shifted_cocg(h.ptr, args["cols"], p.energies, args["eta"], args["tol"], 100, G0)

@@ -1,0 +1,124 @@
+"""GPU parity of the Dyson/OBM boundary step (Eq. sec3-01a, Eqs. sec3-02 ... sec3-06) and of the
+Fisher-Lee transmission (Eq. TF) against the CPU oracle."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import make_problem, small_problem, random_complex_matrices   # noqa: E402
+from oracle.cocg import shifted_cocg_columns                                 # noqa: E402
+from oracle.operator import boundary_rows                                    # noqa: E402
+from oracle.dense import g_dense                                             # noqa: E402
+from oracle.leads import sigma_bloch, open_channels                          # noqa: E402
+from oracle.dyson import dyson_solve                                         # noqa: E402
+from oracle.transmission import transmission                                 # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_00081_gb300.build_lib import build
+    build()
+    import paper_1502_00081_gb300 as m
+    m.load_library()
+    return m
+
+
+def _abi(M):
+    """[K, rows, cols] matrices -> contiguous column-major ABI layout on the GPU."""
+    return torch.from_numpy(np.ascontiguousarray(M.transpose(0, 2, 1))).cuda()
+
+
+def _mat(t):
+    return t.cpu().numpy().astype(np.complex128).transpose(0, 2, 1)
+
+
+@pytest.mark.parametrize("nb", [16, 70, 128])
+def test_dyson_random_matrices(rs, nb):
+    """Dyson solve on seeded random complex-symmetric G0 and Sigma (retarded sign), FP64 handle."""
+    K, ns = 3, nb // 2
+    G0 = random_complex_matrices(nb, K, seed=11, scale=0.5)
+    SL = random_complex_matrices(ns, K, seed=12, scale=0.5, imag_sign=-1)
+    SR = random_complex_matrices(ns, K, seed=13, scale=0.5, imag_sign=-1)
+    # a handle whose boundary set has nb rows: nf=1 plane of nb/2 points per side
+    nx = ns
+    with rs.Handle((nx, 1, 4), 0.5, 2, np.zeros(nx * 4), n_face=1, precision=rs.RSFD_FP64) as h:
+        assert h.nb == nb
+        G = torch.empty((K, nb, nb), dtype=torch.complex128, device="cuda")
+        ref = rs.rsfd_dyson_boundary(h.ptr, _abi(G0), _abi(SL), _abi(SR), G)
+        Gg = _mat(G)
+        T = rs.rsfd_transmission(h.ptr, G, _abi(SL), _abi(SR))
+    for k in range(K):
+        Go = dyson_solve(G0[k], SL[k], SR[k])
+        assert np.linalg.norm(Gg[k] - Go) / np.linalg.norm(Go) <= 1e-10
+        assert abs(T[k] - transmission(Go, SL[k], SR[k])[0]) <= 1e-9 * max(1.0, abs(T[k]))
+    assert (ref < 1e-12).all()
+
+
+def test_tiny_wire_end_to_end_fp64(rs):
+    """G0_bb (shifted COCG) -> host Sigma -> Dyson -> T on the 8x8x12 wire, against the dense
+    (Z - H - Sigma)^{-1} of the oracle."""
+    p = make_problem("tiny_wire_fp64")
+    b = boundary_rows(p.grid, p.n_face)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_FP64) as h:
+        G0 = torch.zeros((p.K, h.nb, h.nb), dtype=torch.complex128, device="cuda")
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, p.tol, p.maxit, G0)
+        assert st == rs.RSFD_OK
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+        SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
+        G = torch.empty_like(G0)
+        rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
+        T = rs.rsfd_transmission(h.ptr, G, SL, SR)
+        Gg = _mat(G)
+    for k, E in enumerate(p.energies):
+        Z = E + 1j * p.eta
+        SLo, SRo = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
+        Gd = g_dense(p, Z, SLo, SRo, rows=b, cols=b)
+        assert np.linalg.norm(Gg[k] - Gd) / np.linalg.norm(Gd) <= 1e-9
+        To = transmission(Gd, SLo, SRo)[0]
+        assert abs(T[k] - To) <= 1e-9
+        assert -1e-6 <= T[k] <= open_channels(p.grid[0], p.grid[1], p.h, p.fd_order, E) + 1e-2
+
+
+@pytest.mark.parametrize("order,E,n_open", [(2, 3.0, 1), (4, 8.0, 3)])
+def test_uniform_wire_integer_channels(rs, order, E, n_open):
+    """V = 0 wire: T equals the open-channel count as eta -> 0 (GPU COCG + Dyson + T)."""
+    p = small_problem(grid=(3, 3, 8), h=0.5, fd_order=order, n_wells=0, n_energies=1, e_range=(E, E),
+                      eta=1e-7, tol=1e-13)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, precision=rs.RSFD_FP64) as h:
+        G0 = torch.zeros((1, h.nb, h.nb), dtype=torch.complex128, device="cuda")
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, p.tol, 20000, G0)
+        assert st == rs.RSFD_OK
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(3, 3, p.h, order, p.energies, p.eta)
+        SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
+        G = torch.empty_like(G0)
+        rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
+        T = rs.rsfd_transmission(h.ptr, G, SL, SR)
+    assert abs(T[0] - n_open) < 1e-4
+
+
+def test_mixed_handle_dyson_T(rs):
+    """Mixed-precision handle: complex64 G0_bb from the COCG, FP64 Dyson with refinement, T."""
+    p = small_problem(grid=(10, 8, 16), h=0.45, fd_order=4, n_wells=3, n_energies=6, e_range=(1.0, 3.0),
+                      eta=1e-2, tol=1e-7)
+    b = boundary_rows(p.grid, p.n_face)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, precision=rs.RSFD_MIXED) as h:
+        G0 = torch.zeros((p.K, h.nb, h.nb), dtype=torch.complex64, device="cuda")
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, p.tol, p.maxit, G0)
+        assert st == rs.RSFD_OK
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+        SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
+        G = torch.empty_like(G0)
+        rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
+        T = rs.rsfd_transmission(h.ptr, G, SL, SR)
+        Gg = _mat(G)
+    for k, E in enumerate(p.energies):
+        Z = E + 1j * p.eta
+        SLo, SRo = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
+        Gd = g_dense(p, Z, SLo, SRo, rows=b, cols=b)
+        assert np.linalg.norm(Gg[k] - Gd) / np.linalg.norm(Gd) <= 1e-5
+        assert abs(T[k] - transmission(Gd, SLo, SRo)[0]) <= 1e-4
