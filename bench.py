@@ -1,0 +1,386 @@
+"""Benchmark: shifted-COCG Green's-function columns x energies per second on GB300.
+
+One step = one call of the library's shifted COCG (rsfd_shifted_cocg) over the whole
+"sampled_columns_mixed" workload: a 64x64x128 grid, h = 0.4 bohr, 4th-order stencil, 200
+seeded Gaussian wells, 256 unit right-hand sides sampled from the two outer planes and 128
+energies in [-0.5, 0.5] Ha with eta = 1e-3 Ha, mixed precision (complex64 Krylov vectors, FP64
+scalars and reductions), tolerance 1e-6.  Every seed SpMV, seed update, dot product, scalar
+recurrence, shift update and the G0_bb write-out of the step runs in the library's kernels.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead (bounded
+sample, see below).  Under torchrun (N > 1) every rank solves its own 256 columns (weak scaling,
+no collective on the data path); the step time is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "sampled_columns_mixed"
+METRIC = "greens_fn_columns_x_energies_per_s"
+UNIT = "columns*energies/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if _cuda() else "gloo")
+    return world, rank, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def rank_columns(p, rank):
+    """Columns of one rank: the workload's own sample on rank 0, a rank-specific sample otherwise."""
+    from workloads import sample_plane_columns
+    if rank == 0:
+        return p.cols
+    return sample_plane_columns(p.grid, p.cols.size, seed=p.seed + 7919 * rank)
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle leg (bounded sample)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(p, budget_s=15.0):
+    """Time the oracle's shifted COCG (as it stands) on one column of the workload for a bounded
+    number of iterations; return seconds per seed iteration and the sample description."""
+    from oracle.cocg import shifted_cocg
+    from oracle.operator import hamiltonian, apply_h, boundary_rows
+    Hloc, P, wE = hamiltonian(p)
+    rows = boundary_rows(p.grid, p.n_face)
+    Z = p.energies + 1j * p.eta
+    b = np.zeros(p.N, np.complex128)
+    b[int(p.cols[0])] = 1.0
+    f = lambda v: apply_h(Hloc, P, wE, v)
+    t0 = time.perf_counter()
+    shifted_cocg(f, b, Z, p.tol, rows=rows, maxit=5)
+    t_probe = (time.perf_counter() - t0) / 5.0
+    iters = max(10, int(budget_s / max(t_probe, 1e-6)))
+    t0 = time.perf_counter()
+    r = shifted_cocg(f, b, Z, p.tol, rows=rows, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt / max(r.iterations, 1), r.iterations, dt
+
+
+def _oracle_iterations_per_column(p):
+    """Seed iterations per column of this workload, as stored by tests/golden/make_golden.py from
+    the oracle itself (None when absent)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{p.name}_oracle_iterations.json")
+    if os.path.exists(path):
+        return json.load(open(path))
+    return None
+
+
+def cpu_baseline_line(p, budget_s, gpu_mean_iters=None):
+    t_it, n_it, dt = oracle_sample(p, budget_s)
+    stored = _oracle_iterations_per_column(p)
+    if stored is not None:
+        iters_per_col, src = float(stored["mean_iterations"]), "oracle's own iteration count (tests/golden)"
+    elif gpu_mean_iters is not None:
+        iters_per_col, src = float(gpu_mean_iters), "mean iteration count of this run"
+    else:
+        iters_per_col, src = float("nan"), "unknown"
+    value = p.K / (t_it * iters_per_col)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 column x {p.K} energies, first {n_it} seed iterations ({dt:.1f} s, numpy/scipy "
+                       f"single-threaded, host nproc={os.cpu_count()}), scaled to {iters_per_col:.0f} "
+                       f"iterations per column ({src})")}
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import make_problem
+
+    world, rank, local = _dist_init()
+    torch.cuda.set_device(local)
+    rs.load_library()
+    p = make_problem(args.workload)
+    if args.precision:
+        p.precision = args.precision
+    if args.ncols:
+        p.cols = p.cols[:args.ncols]
+    cols = rank_columns(p, rank)
+    if args.ncols:
+        cols = cols[:args.ncols]
+    prec = rs.RSFD_MIXED if p.precision == "mixed" else rs.RSFD_FP64
+    vsz = 8 if prec == rs.RSFD_MIXED else 16
+    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
+    rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, profile=1)
+    G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, p.tol, p.maxit, G0)
+        return st, info
+
+    for _ in range(args.warmup):
+        st, info = step()
+    # timed region
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    _barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    agg = {"ms_pass": 0.0, "ms_shift": 0.0, "slot_iterations": 0, "shift_updates": 0, "n_pass": 0, "n_shift": 0,
+           "n_other": 0}
+    statuses, iters = [], []
+    for _ in range(args.steps):
+        st, info = step()
+        statuses.append(st)
+        iters.append(float(info["iters"].mean()))
+        s = rs.rsfd_get_stats(h.ptr)
+        for k in agg:
+            agg[k] += s[k]
+        slots_used = s["slots"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop() if sampler else None
+    ms_max = _max_over_ranks(ms, world)
+    units = _sum_over_ranks(float(cols.size * p.K * args.steps), world)
+    value = units / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (algorithmic bytes / summed event-timed duration)
+    N, nb, K = p.N, h.nb, p.K
+    pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + agg["n_pass"] * 4 * N
+    shift_bytes = agg["shift_updates"] * 4 * vsz * nb + agg["slot_iterations"] * vsz * nb
+    peak, peak_src = _peaks()
+    kern = {"pass": (pass_bytes, agg["ms_pass"]), "shift": (shift_bytes, agg["ms_shift"])}
+    dom = max(kern, key=lambda k: kern[k][1])
+    dbytes, dms = kern[dom]
+    achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(dom)
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers: V_loc from pinned host memory into a new
+    # handle, the solve, and G0_bb back into pinned host memory, every step
+    e2e = None
+    if not args.no_e2e:
+        Vh = torch.from_numpy(np.ascontiguousarray(p.V.ravel())).pin_memory()
+        Gh = torch.empty(G0.shape, dtype=G0.dtype).pin_memory()
+        e_steps = max(1, args.e2e_steps)
+        _barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            h2 = rs.Handle(p.grid, p.h, p.fd_order, Vh.numpy(), n_face=p.n_face, precision=prec)
+            rs.rsfd_set_solve_options(h2.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync)
+            G2 = torch.empty_like(G0)
+            rs.rsfd_shifted_cocg(h2.ptr, cols, p.energies, p.eta, p.tol, p.maxit, G2)
+            Gh.copy_(G2, non_blocking=True)
+            torch.cuda.synchronize()
+            h2.close()
+            del G2
+        dt = time.perf_counter() - t0
+        dt_max = _max_over_ranks(dt, world)
+        e_units = _sum_over_ranks(float(cols.size * p.K * e_steps), world)
+        e2e = {"value": e_units / dt_max, "unit": UNIT, "h2d_bytes_per_step": int(Vh.numel() * 8 + cols.size * 8 + K * 8),
+               "d2h_bytes_per_step": int(Gh.numel() * Gh.element_size()), "steps": e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_line(p, args.cpu_budget, gpu_mean_iters=statistics.mean(iters))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64+f64" if prec == rs.RSFD_MIXED else "c128", "data": "synthetic",
+        "config": {"workload": p.name, "grid": list(p.grid), "h": p.h, "fd_order": p.fd_order,
+                   "columns_per_gpu": int(cols.size), "energies": K, "eta": p.eta, "tol": p.tol,
+                   "precision": p.precision, "boundary_rows": nb, "slots": slots_used,
+                   "l2": "inputs larger than L2 (Krylov vectors of all slots: "
+                         f"{3 * vsz * N * slots_used / 1e6:.0f} MB > 126 MB)",
+                   "parallelism": f"columns over {world} GPU(s), no collective"},
+        "status": [int(x) for x in statuses], "mean_iterations_per_column": statistics.mean(iters),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": peak_src,
+                     "kernels": {k: {"alg_bytes": v[0], "ms": v[1],
+                                     "GBps": (v[0] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None}
+                                 for k, v in kern.items()}},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(agg["n_pass"] + agg["n_shift"] + agg["n_other"]),
+    }
+    print(json.dumps(out), flush=True)
+    h.close()
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is a bounded sample of the workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workloads import make_problem
+    p = make_problem(args.workload)
+    budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(p, budget_s=min(budget, 5.0))
+    vals, descr = [], None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        line = cpu_baseline_line(p, budget)
+        vals.append(line["value"])
+        descr = line
+    dt = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": p.name, "grid": list(p.grid), "energies": p.K, "columns_per_gpu": int(p.cols.size)},
+           "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descr["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--ncols", type=int, default=0, help="use only the first n columns (quick runs)")
+    ap.add_argument("--slots", type=int, default=0)
+    ap.add_argument("--iters-per-sync", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -101,7 +101,8 @@ typedef struct {
                              multiple of 32 and <= 640 (RSFD_ERR_ARG otherwise) */
   int32_t z_chunk;        /* planes per CTA along z */
   int32_t use_graphs;     /* 1 = capture iteration chunks in CUDA graphs (default), -1 = plain launches */
-  int32_t profile;        /* 1 = time every kernel launch with CUDA events (rsfd_get_stats) */
+  int32_t profile;        /* 1 = time every kernel launch with CUDA events on the launching stream
+                             (event nodes inside the CUDA graph); results in rsfd_get_stats */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

@@ -60,6 +60,49 @@ template <> struct VOps<double> {
   static __device__ __forceinline__ C from(double2 z) { return z; }
 };
 
+// Per-thread dot-product accumulators: (r,r), (r,Ar) unconjugated and ||r||^2.
+template <typename T> struct Acc;
+
+template <> struct Acc<double> {
+  double rr_x = 0, rr_y = 0, ra_x = 0, ra_y = 0, nn = 0;
+  __device__ __forceinline__ void add(double2 r, double2 v) {
+    rr_x = fma(r.x, r.x, fma(-r.y, r.y, rr_x));
+    rr_y = fma(2.0 * r.x, r.y, rr_y);
+    ra_x = fma(r.x, v.x, fma(-r.y, v.y, ra_x));
+    ra_y = fma(r.x, v.y, fma(r.y, v.x, ra_y));
+    nn = fma(r.x, r.x, fma(r.y, r.y, nn));
+  }
+  __device__ __forceinline__ void get(double* o) const { o[0] = rr_x; o[1] = rr_y; o[2] = ra_x; o[3] = ra_y; o[4] = nn; }
+};
+
+template <> struct Acc<float> {
+  float2 rr = make_float2(0.f, 0.f), rr_c = make_float2(0.f, 0.f);   // Kahan sum and compensation
+  float2 ra = make_float2(0.f, 0.f), ra_c = make_float2(0.f, 0.f);
+  float nn = 0.f;
+  static __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+  static __device__ __forceinline__ void kahan(float2& s, float2& c, float2 term) {
+    const float2 y = sub2(term, c);
+    const float2 t = __fadd2_rn(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void add(float2 r, float2 v) {
+    // r*r = (x^2 - y^2, 2xy);  r*v = (x vx - y vy, x vy + y vx)
+    const float2 trr = make_float2(__fmaf_rn(r.x, r.x, -r.y * r.y), 2.f * r.x * r.y);
+    const float2 tra = make_float2(__fmaf_rn(r.x, v.x, -r.y * v.y), __fmaf_rn(r.x, v.y, r.y * v.x));
+    kahan(rr, rr_c, trr);
+    kahan(ra, ra_c, tra);
+    nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
+  }
+  __device__ __forceinline__ void get(double* o) const {
+    o[0] = (double)rr.x - (double)rr_c.x;
+    o[1] = (double)rr.y - (double)rr_c.y;
+    o[2] = (double)ra.x - (double)ra_c.x;
+    o[3] = (double)ra.y - (double)ra_c.y;
+    o[4] = (double)nn;
+  }
+};
+
 struct PassParams {
   SolveDims d;
   void* rbuf;
@@ -185,7 +228,9 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
       double2 beta = make_double2(0.0, 0.0);
       double2 rr = S.rr, rAr = S.rAr;
       double2 alpha_prev = st->alpha_prev;
-      double2 scale_n = make_double2(1.0, 0.0), scale_nm1 = make_double2(1.0, 0.0);
+      // stored vectors: r_n is in the current normalisation, r_{n-1} needs the factor carried
+      // over from a switch in the previous step (collinear rescaling, Eq. seedswitch)
+      double2 scale_n = make_double2(1.0, 0.0), scale_nm1 = st->carry;
       if (n > 0) beta = cdiv(rr, st->rr_prev);                                   // Eq. beta
       if (b_all) {
         st->status = SLOT_BREAKDOWN;
@@ -208,7 +253,7 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
           rAr = cdiv(cadd(rAr, cmul(csub(p.Z[s2], p.Z[seed]), rr)), f2);         // (r~, (Z_s~ - H) r~)
           rr = cdiv(rr, f2);
           scale_n = cdiv(make_double2(1.0, 0.0), fn);
-          scale_nm1 = cdiv(make_double2(1.0, 0.0), fnm1);
+          scale_nm1 = cdiv(scale_nm1, fnm1);
           S.fn = fn;
           S.fnm1 = fnm1;
           S.do_switch = 1;
@@ -281,6 +326,7 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
     st->seed = S.seed;
     st->alpha_prev = S.alpha;
     st->rr_prev = S.rr;
+    st->carry = S.scale_n;   // r_n becomes the next step's r_{n-1}
     st->k4_n = S.n;
     st->n = S.n + 1;
     atomicAdd(&p.counters[1], 1ull);
@@ -345,7 +391,10 @@ __global__ void __launch_bounds__(640) pass_kernel(PassParams p) {
     const int z = z0 - 2 * R + k - 1;
     if (inside && z >= 0 && z < d.nz) qa[k] = rm1[z * nxy + coff];
   }
-  T acc_rr_x = 0, acc_rr_y = 0, acc_ra_x = 0, acc_ra_y = 0, acc_nn = 0;
+  // Per-thread partial sums of (r,r) and (r,Ar).  The unconjugated forms cancel, so in FP32 they
+  // are accumulated with Kahan compensation (plain FP32 accumulation of FP32 products makes some
+  // columns stagnate); ||r||^2 has no cancellation and is summed plainly.
+  Acc<T> acc;
   int buf = 0;
 
   for (int pz = z0 - R; pz < z1 + R; ++pz) {
@@ -413,18 +462,15 @@ __global__ void __launch_bounds__(640) pass_kernel(PassParams p) {
       dg.x = zre - vq[0];
       dg.y = zim;
       v = O::fmac(dg, r, v);
-      acc_rr_x = fma(r.x, r.x, fma(-r.y, r.y, acc_rr_x));
-      acc_rr_y = fma((T)2 * r.x, r.y, acc_rr_y);
-      acc_ra_x = fma(r.x, v.x, fma(-r.y, v.y, acc_ra_x));
-      acc_ra_y = fma(r.x, v.y, fma(r.y, v.x, acc_ra_y));
-      acc_nn = fma(r.x, r.x, fma(r.y, r.y, acc_nn));
+      acc.add(r, v);
       rout[zo * nxy + coff] = r;
     }
     buf ^= 1;
   }
 
   // per-CTA partial sums, promoted to FP64 for the tree
-  double v5[5] = {(double)acc_rr_x, (double)acc_rr_y, (double)acc_ra_x, (double)acc_ra_y, (double)acc_nn};
+  double v5[5];
+  acc.get(v5);
   block_sum<5>(v5, S.red);
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   if (tid == 0) {
@@ -573,6 +619,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
     s.Zs = p.Z[p.seed0];
     s.alpha_prev = make_double2(1.0, 0.0);   // alpha_{-1} = 1
     s.rr_prev = make_double2(1.0, 0.0);
+    s.carry = make_double2(1.0, 0.0);
     p.slots[slot] = s;
   }
 }

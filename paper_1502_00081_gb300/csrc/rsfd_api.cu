@@ -310,7 +310,8 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   }
   d.W = W;
   const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
-  const bool use_graphs = h->opts.use_graphs >= 0 && !h->opts.profile;
+  // profiling inside graphs records external event nodes around every launch of the chunk
+  const bool use_graphs = h->opts.use_graphs >= 0;
 
   // ---- workspace
   rsfd_status s;
@@ -405,13 +406,16 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
     pev.resize(4 * C);
     for (auto& e : pev) RSFD_CK(h, cudaEventCreate(&e));
   }
+  auto rec = [&](cudaEvent_t e) -> cudaError_t {
+    return use_graphs ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+  };
   auto issue_chunk = [&]() -> rsfd_status {
     for (int t = 0; t < C; ++t) {
-      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 0], st));
+      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 0]));
       RSFD_CK(h, launch_pass(fp64, d, b, coef, tol, maxit, st));
-      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 1], st));
+      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 1]));
       RSFD_CK(h, launch_shift(fp64, d, b, st));
-      if (h->opts.profile) RSFD_CK(h, cudaEventRecord(pev[4 * t + 2], st));
+      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 2]));
     }
     return RSFD_OK;
   };

@@ -67,6 +67,7 @@ struct __align__(16) SlotState {
   double2 Zs;         // seed energy used by the next pass (A = Zs - H)
   double2 alpha_prev; // alpha_{n-1}
   double2 rr_prev;    // (r_{n-1}, r_{n-1}) in the current seed's normalisation
+  double2 carry;      // factor that brings the stored r_{n-1} to the current seed's normalisation
 };
 
 // Per (slot, energy) scalars (FP64).

@@ -21,5 +21,6 @@ from .problems import (  # noqa: F401
     small_problem,
     grid_coordinates,
     boundary_plane_points,
+    sample_plane_columns,
     random_complex_matrices,
 )

@@ -192,6 +192,11 @@ def _peapod_sites(rng, grid, h):
     return np.asarray(sites)
 
 
+def sample_plane_columns(grid, n_cols, seed):
+    """n_cols distinct points drawn uniformly from the planes z=0 and z=Nz-1 (sorted), seeded."""
+    return _sample_plane_columns(np.random.Generator(np.random.PCG64(seed)), grid, n_cols)
+
+
 def _sample_plane_columns(rng, grid, n_cols):
     nx, ny, nz = grid
     pool = boundary_plane_points(grid, [0, nz - 1])
