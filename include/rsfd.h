@@ -188,6 +188,35 @@ rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma
 rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double h, int32_t fd_order, const double* energies,
                                     double eta, int32_t K, double* Sigma_L, double* Sigma_R);
 
+/* Size of the file-scope device array that rsfd_dyson_boundary_noalloc uses as scratch. */
+#define RSFD_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Allocation-free Dyson step.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory when they need the step, e.g. code recording a CUDA graph
+ * (no cudaMalloc during stream capture), a service whose device memory is already handed to
+ * another allocator, or a library that must not change the device's allocation state.
+ *
+ * It computes the same result as rsfd_dyson_boundary for FP64 data, without a handle:
+ *   (I - G0_bb(k) Sigma_bb(k)) G_bb(k) = G0_bb(k),  k < K,  with two FP64 refinement steps.
+ *   nb      even, the number of boundary rows (ns = nb/2 per slab).
+ *   G0_bb   device [K][nb][nb] c128, column-major per energy (same layout as rsfd_dyson_boundary).
+ *   Sigma_L, Sigma_R  device [K][ns][ns] c128.
+ *   G_bb    device output [K][nb][nb] c128 (may not alias G0_bb).
+ *   refine_residual  host [K] (nullable): ||G0 - M G||_F / ||G0||_F.
+ *   stream  cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ * Scratch: a static __device__ array of RSFD_NOALLOC_SCRATCH_BYTES (32 MiB) held by every GPU that
+ * loads the library until the process exits.  The call needs 3*nb*nb*K*16 bytes plus pivots and
+ * returns RSFD_ERR_ARG (with a message naming the limit) when that exceeds the array; for nb = 128
+ * that allows K <= 42.  Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Sharing: every call, on any stream, uses the same array and it keeps the previous call's
+ * contents (the call clears what must start at zero); calls that overlap on the GPU race with
+ * each other, so serialise them.
+ * Returns RSFD_OK, RSFD_ERR_ARG, RSFD_ERR_CUDA, or RSFD_ERR_BREAKDOWN (singular I - G0 Sigma). */
+rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L,
+                                        const void* Sigma_R, void* G_bb, double* refine_residual, void* stream);
+
 /* Message of the last failure on this handle (h = NULL: last failure of a call
  * without a handle, e.g. rsfd_create).  Never NULL. */
 const char* rsfd_last_error(rsfd_handle h);

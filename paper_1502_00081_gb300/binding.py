@@ -78,6 +78,8 @@ _SIGNATURES = {
     "rsfd_lead_sigma_uniform": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_dyson_boundary_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                                   ctypes.POINTER(ctypes.c_double), _P]),
     "rsfd_last_error": (ctypes.c_char_p, [_P]),
     "rsfd_destroy": (None, [_P]),
 }
@@ -218,6 +220,22 @@ def rsfd_dyson_boundary(h, G0_bb, Sigma_L, Sigma_R, G_bb):
     pg = _dev_ptr(G_bb, (G0_bb.dtype,), tuple(G0_bb.shape), name="G_bb")
     ref = np.zeros(K, np.float64)
     _check(h, lib.rsfd_dyson_boundary(h, p0, pl, pr, K, pg, ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return ref
+
+
+def rsfd_dyson_boundary_noalloc(G0_bb, Sigma_L, Sigma_R, G_bb, stream=None):
+    """Allocation-free Dyson step (c128 data, no handle); returns the refinement residuals."""
+    import torch
+    lib = load_library()
+    K, nb = int(G0_bb.shape[0]), int(G0_bb.shape[-1])
+    p0 = _dev_ptr(G0_bb, (torch.complex128,), name="G0_bb")
+    pl = _dev_ptr(Sigma_L, (torch.complex128,), name="Sigma_L")
+    pr = _dev_ptr(Sigma_R, (torch.complex128,), name="Sigma_R")
+    pg = _dev_ptr(G_bb, (torch.complex128,), tuple(G0_bb.shape), name="G_bb")
+    ref = np.zeros(K, np.float64)
+    st = lib.rsfd_dyson_boundary_noalloc(nb, K, p0, pl, pr, pg, ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         _stream_ptr(stream))
+    _check(None, st)
     return ref
 
 

@@ -381,3 +381,121 @@ rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const voi
 }
 
 }  // namespace rsfd
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free variant of the Dyson step.
+//
+// Some callers cannot allocate device memory at the point where they need the Dyson step: a
+// program that is recording a CUDA graph (cudaMalloc is not allowed while a stream is being
+// captured), a service that has handed its whole device-memory budget to another allocator up
+// front, or a library that must not change the device's allocation state.  For them,
+// rsfd_dyson_boundary_noalloc keeps its scratch (the matrices I - G0 Sigma and their LU factors,
+// the refinement residual, the pivots) in the file-scope device array below, which exists for as
+// long as the library is loaded on every GPU that loaded it.  The caller passes the inputs and the
+// output; nothing is allocated by the call.
+// ------------------------------------------------------------------------------------------------
+namespace rsfd {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)RSFD_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// device address of g_noalloc_scratch, looked up once per device (host code must not use the
+// symbol itself: on the host it is only a stand-in)
+constexpr int kMaxDevices = 64;
+static void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+__global__ void noalloc_finish(const int* info, const double* red, int K, int* bad, double* ratio) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    if (info[k] != 0) atomicMax(bad, k + 1);
+    const double g = red[K + k] > 0 ? red[K + k] : 1.0;
+    ratio[k] = sqrt(red[k]) / sqrt(g);
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+}  // namespace rsfd
+
+extern "C" rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L,
+                                                   const void* Sigma_R, void* G_bb, double* refine_residual,
+                                                   void* stream) {
+  using namespace rsfd;
+  if (nb < 2 || (nb % 2) != 0 || K < 1 || !G0_bb || !Sigma_L || !Sigma_R || !G_bb || G0_bb == G_bb)
+    return handle_fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_boundary_noalloc: bad arguments");
+  const long long n2 = (long long)nb * nb;
+  const size_t need = 3 * align256((size_t)n2 * K * sizeof(double2)) + align256((size_t)K * (nb + 1) * sizeof(int)) +
+                      align256((size_t)3 * K * sizeof(double)) + align256(sizeof(int));
+  if (need > kNoAllocScratchBytes)
+    return handle_fail(nullptr, RSFD_ERR_ARG,
+                       "rsfd_dyson_boundary_noalloc: 3*nb*nb*K*16 bytes plus pivots exceed the " +
+                           std::to_string(kNoAllocScratchBytes) + "-byte static scratch (nb=" + std::to_string(nb) +
+                           ", K=" + std::to_string(K) + ")");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return handle_fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_boundary_noalloc: device index too large");
+  if (!g_scratch_ptr[dev]) {   // one-time set-up on this device (the current device)
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = p;
+  }
+  unsigned char* base = (unsigned char*)g_scratch_ptr[dev];
+  double2* dM = (double2*)base;
+  base += align256((size_t)n2 * K * sizeof(double2));
+  double2* dLU = (double2*)base;
+  base += align256((size_t)n2 * K * sizeof(double2));
+  double2* dR = (double2*)base;
+  base += align256((size_t)n2 * K * sizeof(double2));
+  int* piv = (int*)base;
+  int* info = piv + (size_t)K * nb;
+  base += align256((size_t)K * (nb + 1) * sizeof(int));
+  double* red = (double*)base;   // [2K] squared norms, [K] ratios
+  base += align256((size_t)3 * K * sizeof(double));
+  int* bad = (int*)base;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const double2* G0 = (const double2*)G0_bb;
+  double2* dX = (double2*)G_bb;
+  const long long tot = n2 * K;
+  const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  // the scratch keeps the previous call's contents: clear the flags that must start at zero
+  e = cudaMemsetAsync(info, 0, K * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+  if (e != cudaSuccess) return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  set_identity<<<grid_for(tot), 256, 0, st>>>(dM, nb, K);
+  const int ns = nb / 2;
+  zgemm(st, K, nb, ns, ns, m1, G0, nb, n2, 0, (const double2*)Sigma_L, ns, (long long)ns * ns, one, dM, nb, n2);
+  zgemm(st, K, nb, ns, ns, m1, G0 + (long long)ns * nb, nb, n2, 0, (const double2*)Sigma_R, ns, (long long)ns * ns, one,
+        dM + (long long)ns * nb, nb, n2);
+  copy_c128<<<grid_for(tot), 256, 0, st>>>(dM, dLU, tot);
+  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  copy_c128<<<grid_for(tot), 256, 0, st>>>(G0, dX, tot);
+  dim3 g((nb + 127) / 128, K);
+  zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dX, nb, nb);
+  for (int it = 0; it < 2; ++it) {
+    copy_c128<<<grid_for(tot), 256, 0, st>>>(G0, dR, tot);
+    zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dR, nb, nb);
+    axpy_c128<<<grid_for(tot), 256, 0, st>>>(dX, dR, tot);
+  }
+  copy_c128<<<grid_for(tot), 256, 0, st>>>(G0, dR, tot);
+  zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+  frob2_batched<<<K, 256, 0, st>>>(dR, n2, red);
+  frob2_batched<<<K, 256, 0, st>>>(G0, n2, red + K);
+  noalloc_finish<<<1, 256, 0, st>>>(info, red, K, bad, red + 2 * K);
+  e = cudaGetLastError();
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && refine_residual)
+    e = cudaMemcpyAsync(refine_residual, red + 2 * K, K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("rsfd_dyson_boundary_noalloc: ") + cudaGetErrorString(e));
+  if (hbad)
+    return handle_fail(nullptr, RSFD_ERR_BREAKDOWN,
+                       "rsfd_dyson_boundary_noalloc: singular I - G0 Sigma at energy " + std::to_string(hbad - 1));
+  return RSFD_OK;
+}
