@@ -25,7 +25,7 @@
  *   left slab, the second half the right slab; ns = nb/2.
  * Complex numbers: interleaved (re, im).  "c64" = 2 x float, "c128" = 2 x double.
  *   The handle's precision picks the element type of G0_bb / G_bb: c128 for
- *   RSFD_FP64, c64 for RSFD_MIXED.
+ *   RSFD_FP64 and RSFD_DF64, c64 for RSFD_MIXED.
  * Matrices: column-major per energy.  G0_bb is [K][ncols][nb]: element
  *   (k, row r, column c) sits at k*nb*ncols + c*nb + r.  Self-energies are
  *   [K][ns][ns] c128 with element (k, a, c) at k*ns*ns + c*ns + a.
@@ -65,7 +65,14 @@ typedef enum {
   RSFD_ERR_UNSUPPORTED = 7    /* valid request that this build does not implement */
 } rsfd_status;
 
-typedef enum { RSFD_FP64 = 0, RSFD_MIXED = 1 } rsfd_precision;
+/* Arithmetic of the shifted COCG:
+ *   RSFD_FP64  complex128 Krylov vectors and FP64 arithmetic throughout.
+ *   RSFD_MIXED complex64 Krylov vectors and SpMV (FP32 arithmetic), FP64 scalar recurrences and
+ *              FP64 reductions (per-thread partial sums Kahan-compensated in FP32).
+ *   RSFD_DF64  "double-float" Krylov vectors (each component an unevaluated sum of two floats,
+ *              about 48 significant bits) with error-free FP32 arithmetic in the SpMV and the
+ *              seed update, FP64 scalars.  Accuracy close to RSFD_FP64 at FP32-pipe speed. */
+typedef enum { RSFD_FP64 = 0, RSFD_MIXED = 1, RSFD_DF64 = 2 } rsfd_precision;
 
 /* Initial seed of the shifted COCG (Appendix; Sec. III C starts from the Fermi energy). */
 typedef enum {
@@ -96,9 +103,10 @@ typedef struct {
 /* Launch options of the solver; zero fields mean "choose automatically". */
 typedef struct {
   int32_t slots;          /* columns iterated together (RHS block width) */
-  int32_t iters_per_sync; /* iterations per CUDA-graph replay between host checks */
-  int32_t tile_y;         /* stencil tile height in y; (32+2*fd_order)*(tile_y+2*fd_order) must be a
-                             multiple of 32 and <= 640 (RSFD_ERR_ARG otherwise) */
+  int32_t iters_per_sync; /* iterations per CUDA-graph replay between host checks; also the number of
+                             iterations collapsed into one shift update (<= 64) */
+  int32_t tile_y;         /* stencil tile height in y; RSFD_ERR_ARG when the CTA would exceed 768 threads
+                             (512 for RSFD_DF64) or 220 KB of shared memory */
   int32_t z_chunk;        /* planes per CTA along z */
   int32_t use_graphs;     /* 1 = capture iteration chunks in CUDA graphs (default), -1 = plain launches */
   int32_t profile;        /* 1 = time every kernel launch with CUDA events on the launching stream
@@ -109,12 +117,12 @@ typedef struct {
 typedef struct {
   double ms_total;            /* wall time of the call on the device stream (events) */
   double ms_pass;             /* summed duration of stencil/seed-update launches (profile = 1) */
-  double ms_shift;            /* summed duration of shift-update launches (profile = 1) */
+  double ms_shift;            /* summed duration of the collapsed shift-update launches (profile = 1) */
   int64_t n_pass;             /* stencil/seed-update launches */
-  int64_t n_shift;            /* shift-update launches */
+  int64_t n_shift;            /* collapsed shift-update launches */
   int64_t n_other;            /* other kernel launches (slot set-up, reductions) */
   int64_t slot_iterations;    /* sum over columns of seed iterations */
-  int64_t shift_updates;      /* sum over iterations of active (column, energy) pairs */
+  int64_t shift_updates;      /* recorded (column, energy, iteration) updates applied */
   int32_t slots;              /* columns in flight that were used */
   int32_t iters_per_sync;
 } rsfd_stats;
@@ -127,7 +135,7 @@ typedef struct {
  *               0 selects fd_order/2 (the planes the lead couples to).
  *   V_loc     = host [N] local potential, linear grid order.
  *   proj      = NULL or the nonlocal projectors (host arrays, copied).
- *   precision = RSFD_FP64 or RSFD_MIXED.
+ *   precision = RSFD_FP64, RSFD_MIXED or RSFD_DF64.
  *   stream    = cudaStream_t for every device operation of this handle.
  * Returns RSFD_ERR_ARG on invalid sizes, RSFD_ERR_ALLOC / RSFD_ERR_CUDA on
  * device failures; *out is NULL unless RSFD_OK. */

@@ -23,6 +23,7 @@ RSFD_ERR_TIMEOUT = 6
 RSFD_ERR_UNSUPPORTED = 7
 RSFD_FP64 = 0
 RSFD_MIXED = 1
+RSFD_DF64 = 2
 RSFD_SEED_MID = 0
 RSFD_SEED_FIRST = 1
 RSFD_SEED_INDEX = 2
@@ -284,7 +285,7 @@ class Handle:
     @property
     def complex_dtype(self):
         import torch
-        return torch.complex128 if self.precision == RSFD_FP64 else torch.complex64
+        return torch.complex64 if self.precision == RSFD_MIXED else torch.complex128
 
     def close(self):
         rsfd_destroy(self.ptr)

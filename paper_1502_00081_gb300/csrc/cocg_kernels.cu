@@ -1,67 +1,261 @@
 // Shifted COCG kernels for sm_103a.
 //
-// One iteration of the seed system (Appendix, Eqs. rvec, alpha, beta) is a single fused pass
-// per right-hand side ("slot"):
+// Seed iteration (Appendix, Eqs. rvec, alpha, beta).  One fused pass per iteration and right-hand
+// side ("slot") computes
 //
-//   r_n = a1 r_{n-1} + a2 r_{n-2} + aA (A r_{n-1}),       A = Z_s - H_T,
-//   (r_n, r_n), (r_n, A r_n) (unconjugated) and ||r_n||^2,
+//   r_n = a1 r_{n-1} + a2 r_{n-2} + aA (A r_{n-1}),     A = Z_s - H_T,
+//   (r_n, r_n), (r_n, A r_n) (unconjugated bilinear form) and ||r_n||^2,
 //
-// computed on a 2.5D tile that marches along z.  Each CTA owns an x-y tile of one slot and a
-// range of z-planes; it loads r_{n-1} on the tile plus a 2R-wide halo, r_{n-2} on the tile plus
-// an R-wide halo, evaluates A r_{n-1} and r_n on the tile plus R, then A r_n on the tile.  The
-// halo work is recomputed rather than stored, so an iteration moves three vectors through HBM
-// (read r_{n-1}, read r_{n-2}, write r_n) instead of the four or five of a stencil-then-update
-// split.  The last CTA of a slot to finish (atomic ticket, no waiting) reduces the per-CTA dot
-// products in a fixed order and runs the FP64 scalar step: convergence of every energy, seed
-// switching (Eq. seedswitch), alpha_n, beta_{n-1}, and the shifted recurrences pi_{n+1},
-// alpha_n^(i), beta_{n-1}^(i) (Eqs. spi, salpha, sbeta).  A second kernel applies the vector
-// part of the shifted update (Eq. endcollinear and the x^(i) update) on the boundary rows only,
-// with r_n^(i) = r_n / pi_n^(s,i) (Eq. collinear).
+// on a 2.5D tile that marches along z.  Each CTA owns a 32-wide x-y tile of one slot and a range
+// of z-planes.  A single thread streams every plane it needs with TMA (cp.async.bulk.tensor) into a
+// shared-memory ring guarded by mbarriers, kDepth planes ahead of the consumers: r_{n-1} on the tile
+// plus a 2R halo, r_{n-2} and V_loc on the same box.  TMA's zero fill outside the tensor gives the
+// Dirichlet walls and the zero ghosts in z for free.  The threads keep each grid column's
+// z-neighbours in registers, evaluate A r_{n-1} and r_n on the tile plus R (the halo is recomputed
+// instead of stored), then A r_n on the tile for the dot products, so an iteration moves three
+// vectors through HBM.  The last CTA of a slot to finish (atomic ticket; nothing waits on another
+// CTA) reduces the per-CTA partial sums in a fixed order and runs the FP64 scalar step: convergence
+// of every energy, seed switching (Eq. seedswitch), alpha_n, beta_{n-1} and the shifted recurrences
+// pi_{n+1}, alpha_n^(i), beta_{n-1}^(i) (Eqs. spi, salpha, sbeta).
 //
-// No kernel waits on another CTA: there are no spin loops anywhere in this file.
+// Shift update (Eq. endcollinear and the x^(i) update) on the boundary rows only, with
+// r_n^(i) = r_n / pi_n^(s,i) (Eq. collinear).  The recurrences p <- cr_t r_t + cb_t p,
+// x <- x + ca_t p are linear in the residuals r_t, so C consecutive steps collapse into
+//   x <- x + e_x p + sum_t W_x[t] r_t,   p <- e_p p + sum_t W_p[t] r_t,
+// with O(C) FP64 coefficients per energy.  The pass kernel records the boundary rows of r_n and the
+// scalar step records (cr, cb, ca) per energy; every C iterations one kernel applies the collapsed
+// update, which reads and writes x_b and p_b once per C iterations instead of every iteration.
+//
+// Precisions (template MODE):
+//   RSFD_FP64  complex128 vectors, FP64 arithmetic.
+//   RSFD_MIXED complex64 vectors, FP32 arithmetic (packed FFMA2), FP64 scalars and reductions.
+//   RSFD_DF64  complex double-float vectors (hi + lo FP32 pairs, ~48-bit significands) with
+//              error-free FP32 arithmetic and FP64 scalars; the A r_n entering the dot products and
+//              the recorded r_b history use the hi parts.
+//
+// Every wait in this file is an mbarrier try_wait with an iteration cap; on expiry the CTA raises an
+// error flag that the host turns into RSFD_ERR_TIMEOUT.  No CTA waits on another CTA.
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "rsfd_internal.cuh"
 
 namespace rsfd {
+size_t pass_smem(int prec, int R, int tile_y);
 namespace {
 
-constexpr int kTileX = 32;
+constexpr int kTileX = 32;       // interior tile width in x
+constexpr int kBoxX = 40;        // TMA box width in grid points (x0 - 4 ... x0 + 35)
+constexpr int kBoxOff = 4;       // the box starts kBoxOff points left of the tile
+constexpr int kDepth = 2;        // bundles (one plane of each input) in flight ahead of the consumers
+constexpr int kStages = kDepth + 1;
+// threads per CTA of the pass kernel (fewer for double-float, which needs more registers per thread)
+template <int MODE> struct MaxThreads { static constexpr int value = 768; };
+template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 512; };
+template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 512; };
+constexpr long long kWaitCap = 1ll << 22;   // try_wait iterations before a wait is declared lost
 
 // ------------------------------------------------------------------------------------------------
-// vector arithmetic on interleaved complex numbers in the precision of the Krylov vectors
+// packed FP32x2 helpers
 // ------------------------------------------------------------------------------------------------
-template <typename T> struct VOps;
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
 
-template <> struct VOps<float> {
-  typedef float2 C;
-  static __device__ __forceinline__ C zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ C add(C a, C b) { return __fadd2_rn(a, b); }
-  // c + s * a, s real (packed FP32x2 FMA)
-  static __device__ __forceinline__ C fmar(float s, C a, C c) { return __ffma2_rn(make_float2(s, s), a, c); }
-  // c + z * a, z complex
-  static __device__ __forceinline__ C fmac(C z, C a, C c) {
-    c = __ffma2_rn(make_float2(z.x, z.x), a, c);
-    return __ffma2_rn(make_float2(-z.y, z.y), make_float2(a.y, a.x), c);
-  }
-  static __device__ __forceinline__ C from(double2 z) { return make_float2((float)z.x, (float)z.y); }
+// complex double-float: value = h + l, component-wise (h = (re_hi, im_hi), l = (re_lo, im_lo))
+struct __align__(16) dfc {
+  float2 h, l;
+};
+struct dfr {   // real double-float coefficient
+  float h, l;
+};
+struct dfz {   // complex double-float coefficient
+  dfr re, im;
 };
 
-template <> struct VOps<double> {
-  typedef double2 C;
-  static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
-  static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
-  static __device__ __forceinline__ C fmar(double s, C a, C c) { return make_double2(fma(s, a.x, c.x), fma(s, a.y, c.y)); }
-  static __device__ __forceinline__ C fmac(C z, C a, C c) {
-    return make_double2(fma(z.x, a.x, fma(-z.y, a.y, c.x)), fma(z.x, a.y, fma(z.y, a.x, c.y)));
+__host__ __device__ __forceinline__ dfr to_dfr(double v) {
+  dfr r;
+  r.h = (float)v;
+  r.l = (float)(v - (double)r.h);
+  return r;
+}
+
+// Knuth's TwoSum and Dekker's FastTwoSum on packed pairs (error-free transformations)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = f2add(a, b);
+  const float2 bb = f2sub(s, a);
+  e = f2add(f2sub(a, f2sub(s, bb)), f2sub(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = f2add(a, b);
+  e = f2sub(b, f2sub(s, a));
+}
+__device__ __forceinline__ dfc df_add(dfc x, dfc y) {
+  float2 s, e;
+  two_sum2(x.h, y.h, s, e);
+  e = f2add(e, f2add(x.l, y.l));
+  dfc r;
+  fast_two_sum2(s, e, r.h, r.l);
+  return r;
+}
+// acc + c * x for a real double-float c applied to both components (exact product via FMA)
+__device__ __forceinline__ dfc df_mar(dfr c, dfc x, dfc acc) {
+  const float2 ch = bc(c.h);
+  const float2 p = f2mul(ch, x.h);
+  float2 e = f2fma(ch, x.h, f2neg(p));
+  e = f2fma(bc(c.l), x.h, e);
+  e = f2fma(ch, x.l, e);
+  dfc prod;
+  fast_two_sum2(p, e, prod.h, prod.l);
+  return df_add(prod, acc);
+}
+__device__ __forceinline__ dfc df_swapneg(dfc x) {   // i * x
+  dfc r;
+  r.h = make_float2(-x.h.y, x.h.x);
+  r.l = make_float2(-x.l.y, x.l.x);
+  return r;
+}
+__device__ __forceinline__ dfr dfr_sub(dfr a, float vh, float vl) {   // a - (vh + vl), scalar
+  const float s = a.h - vh;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (-vh - bb);
+  e += a.l - vl;
+  dfr r;
+  r.h = s + e;
+  r.l = e - (r.h - s);
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------------
+// precision policies
+// ------------------------------------------------------------------------------------------------
+template <int MODE> struct Ops;
+
+template <> struct Ops<RSFD_MIXED> {
+  typedef float2 C;     // Krylov vector element
+  typedef float VT;     // potential element
+  typedef float2 H;     // element of A r_n in the dot products and of the r_b history
+  typedef float HR;     // scalar type of H
+  typedef float Real;
+  typedef float2 Cplx;
+  static __device__ __forceinline__ C zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ C unit() { return make_float2(1.f, 0.f); }
+  static __device__ __forceinline__ C add(C a, C b) { return f2add(a, b); }
+  static __device__ __forceinline__ C mar(Real c, C x, C acc) { return f2fma(bc(c), x, acc); }
+  static __device__ __forceinline__ C mac(Cplx z, C x, C acc) {
+    acc = f2fma(bc(z.x), x, acc);
+    return f2fma(make_float2(-z.y, z.y), make_float2(x.y, x.x), acc);
   }
-  static __device__ __forceinline__ C from(double2 z) { return z; }
+  // acc + (zre - v + i zim) x
+  static __device__ __forceinline__ C diag(Real zre, Real zim, VT v, C x, C acc) {
+    return mac(make_float2(zre - v, zim), x, acc);
+  }
+  static __device__ __forceinline__ H hi(C x) { return x; }
+  static __device__ __forceinline__ HR vhi(VT v) { return v; }
+  static __host__ __device__ __forceinline__ Real real(double v) { return (float)v; }
+  static __host__ __device__ __forceinline__ Cplx cplx(double2 z) { return make_float2((float)z.x, (float)z.y); }
+};
+
+template <> struct Ops<RSFD_FP64> {
+  typedef double2 C;
+  typedef double VT;
+  typedef double2 H;
+  typedef double HR;
+  typedef double Real;
+  typedef double2 Cplx;
+  static __device__ __forceinline__ C zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ C unit() { return make_double2(1.0, 0.0); }
+  static __device__ __forceinline__ C add(C a, C b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ C mar(Real c, C x, C acc) { return make_double2(fma(c, x.x, acc.x), fma(c, x.y, acc.y)); }
+  static __device__ __forceinline__ C mac(Cplx z, C x, C acc) {
+    return make_double2(fma(z.x, x.x, fma(-z.y, x.y, acc.x)), fma(z.x, x.y, fma(z.y, x.x, acc.y)));
+  }
+  static __device__ __forceinline__ C diag(Real zre, Real zim, VT v, C x, C acc) {
+    return mac(make_double2(zre - v, zim), x, acc);
+  }
+  static __device__ __forceinline__ H hi(C x) { return x; }
+  static __device__ __forceinline__ HR vhi(VT v) { return v; }
+  static __host__ __device__ __forceinline__ Real real(double v) { return v; }
+  static __host__ __device__ __forceinline__ Cplx cplx(double2 z) { return z; }
+};
+
+template <> struct Ops<RSFD_DF64> {
+  typedef dfc C;
+  typedef float2 VT;    // (hi, lo) of V
+  typedef float2 H;
+  typedef float HR;
+  typedef dfr Real;
+  typedef dfz Cplx;
+  static __device__ __forceinline__ C zero() {
+    dfc r;
+    r.h = make_float2(0.f, 0.f);
+    r.l = r.h;
+    return r;
+  }
+  static __device__ __forceinline__ C unit() {
+    dfc r;
+    r.h = make_float2(1.f, 0.f);
+    r.l = make_float2(0.f, 0.f);
+    return r;
+  }
+  static __device__ __forceinline__ C add(C a, C b) { return df_add(a, b); }
+  static __device__ __forceinline__ C mar(Real c, C x, C acc) { return df_mar(c, x, acc); }
+  static __device__ __forceinline__ C mac(Cplx z, C x, C acc) {
+    return df_mar(z.re, x, df_mar(z.im, df_swapneg(x), acc));
+  }
+  static __device__ __forceinline__ C diag(Real zre, Real zim, VT v, C x, C acc) {
+    return df_mar(dfr_sub(zre, v.x, v.y), x, df_mar(zim, df_swapneg(x), acc));
+  }
+  static __device__ __forceinline__ H hi(C x) { return x.h; }
+  static __device__ __forceinline__ HR vhi(VT v) { return v.x; }
+  static __host__ __device__ __forceinline__ Real real(double v) { return to_dfr(v); }
+  static __host__ __device__ __forceinline__ Cplx cplx(double2 z) {
+    dfz r;
+    r.re = to_dfr(z.x);
+    r.im = to_dfr(z.y);
+    return r;
+  }
+};
+
+// arithmetic on the "hi" element H (A r_n for the dot products, history, collapsed update)
+template <typename HR> struct HOps;
+template <> struct HOps<float> {
+  typedef float2 H;
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return f2add(a, b); }
+  static __device__ __forceinline__ float2 mar(float c, float2 x, float2 acc) { return f2fma(bc(c), x, acc); }
+  static __device__ __forceinline__ float2 mac(float2 z, float2 x, float2 acc) {
+    acc = f2fma(bc(z.x), x, acc);
+    return f2fma(make_float2(-z.y, z.y), make_float2(x.y, x.x), acc);
+  }
+  static __device__ __forceinline__ float2 diag(float zre, float zim, float v, float2 x, float2 acc) {
+    return mac(make_float2(zre - v, zim), x, acc);
+  }
+  static __device__ __forceinline__ float2 from(double2 z) { return make_float2((float)z.x, (float)z.y); }
+};
+template <> struct HOps<double> {
+  typedef double2 H;
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ double2 mar(double c, double2 x, double2 acc) {
+    return make_double2(fma(c, x.x, acc.x), fma(c, x.y, acc.y));
+  }
+  static __device__ __forceinline__ double2 mac(double2 z, double2 x, double2 acc) {
+    return make_double2(fma(z.x, x.x, fma(-z.y, x.y, acc.x)), fma(z.x, x.y, fma(z.y, x.x, acc.y)));
+  }
+  static __device__ __forceinline__ double2 diag(double zre, double zim, double v, double2 x, double2 acc) {
+    return mac(make_double2(zre - v, zim), x, acc);
+  }
+  static __device__ __forceinline__ double2 from(double2 z) { return z; }
 };
 
 // Per-thread dot-product accumulators: (r,r), (r,Ar) unconjugated and ||r||^2.
-template <typename T> struct Acc;
+template <typename HR> struct Acc;
 
 template <> struct Acc<double> {
   double rr_x = 0, rr_y = 0, ra_x = 0, ra_y = 0, nn = 0;
@@ -75,19 +269,19 @@ template <> struct Acc<double> {
   __device__ __forceinline__ void get(double* o) const { o[0] = rr_x; o[1] = rr_y; o[2] = ra_x; o[3] = ra_y; o[4] = nn; }
 };
 
+// The unconjugated forms cancel, so in FP32 they are accumulated with Kahan compensation (plain
+// FP32 accumulation of FP32 products makes some columns stagnate); ||r||^2 has no cancellation.
 template <> struct Acc<float> {
-  float2 rr = make_float2(0.f, 0.f), rr_c = make_float2(0.f, 0.f);   // Kahan sum and compensation
+  float2 rr = make_float2(0.f, 0.f), rr_c = make_float2(0.f, 0.f);
   float2 ra = make_float2(0.f, 0.f), ra_c = make_float2(0.f, 0.f);
   float nn = 0.f;
-  static __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
   static __device__ __forceinline__ void kahan(float2& s, float2& c, float2 term) {
-    const float2 y = sub2(term, c);
-    const float2 t = __fadd2_rn(s, y);
-    c = sub2(sub2(t, s), y);
+    const float2 y = f2sub(term, c);
+    const float2 t = f2add(s, y);
+    c = f2sub(f2sub(t, s), y);
     s = t;
   }
   __device__ __forceinline__ void add(float2 r, float2 v) {
-    // r*r = (x^2 - y^2, 2xy);  r*v = (x vx - y vy, x vy + y vx)
     const float2 trr = make_float2(__fmaf_rn(r.x, r.x, -r.y * r.y), 2.f * r.x * r.y);
     const float2 tra = make_float2(__fmaf_rn(r.x, v.x, -r.y * v.y), __fmaf_rn(r.x, v.y, r.y * v.x));
     kahan(rr, rr_c, trr);
@@ -103,36 +297,58 @@ template <> struct Acc<float> {
   }
 };
 
-struct PassParams {
-  SolveDims d;
-  void* rbuf;
-  const void* V;
-  SlotState* slots;
-  ShiftState* shifts;
-  double* partials;
-  unsigned int* tickets;
-  const double2* Z;
-  unsigned long long* counters;
-  double hd;
-  double hk1, hk2;
-  double tol;
-  int maxit;
-};
+// ------------------------------------------------------------------------------------------------
+// mbarrier / TMA primitives (inline PTX)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false when the cap is reached
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitCap; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
 
 // ------------------------------------------------------------------------------------------------
-// block reductions (FP64)
+// reductions (FP64)
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-
-// Sum NV doubles over the block; result valid in thread 0.  s_red must hold 32*NV doubles.
+// Sum NV doubles over the (whole-warp) block; result valid in thread 0.  s_red holds 32*NV doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* s_red) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
-  const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0) {
@@ -142,13 +358,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* s_red) {
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = (lane < nw) ? s_red[lane * NV + k] : 0.0;
-      v[k] = warp_sum(t);
-    }
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum((lane < nw) ? s_red[lane * NV + k] : 0.0);
   }
   __syncthreads();
 }
+
+struct PassParams {
+  SolveDims d;
+  void* rbuf;                // [W][3][Nz][Ny][Nxp] C
+  void* rhist;               // [W][hist_len][nb] H
+  SlotState* slots;
+  ShiftState* shifts;
+  ShiftCoef* coef;           // [W][K][hist_len]
+  double* partials;
+  unsigned int* tickets;
+  const double2* Z;
+  unsigned long long* counters;
+  int* error_flag;
+  double hd;
+  double hk1, hk2;
+  double tol;
+  int maxit;
+  int hist_len;
+};
 
 // ------------------------------------------------------------------------------------------------
 // FP64 scalar step of one slot (run by the last CTA of the slot)
@@ -157,17 +389,18 @@ struct ScalarShared {
   double2 rr, rAr;
   double nrm2;
   double2 beta, alpha, c, scale_n, scale_nm1, fn, fnm1, Zs;
-  int stop;      // 1 = slot finished in this step
+  int stop;
   int do_switch;
   int seed;
   int n;
+  int hc;
   double red[32 * 5];
   int ired[32 * 2];
 };
 
 __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
   const int K = p.d.K;
   SlotState* st = p.slots + slot;
   ShiftState* sh = p.shifts + (size_t)slot * K;
@@ -195,7 +428,6 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
       if (res > best) { best = res; best_i = i; }
     }
   }
-  // block reductions: count, NaN flag, argmax (ties -> lowest index)
   {
     const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
     for (int o = 16; o > 0; o >>= 1) {
@@ -221,7 +453,6 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
         b_all |= v >> 30;
         if (S.red[w] > bb || (S.red[w] == bb && S.ired[w] < bi)) { bb = S.red[w]; bi = S.ired[w]; }
       }
-      // decide what this step does
       int seed = st->seed;
       S.stop = 0;
       S.do_switch = 0;
@@ -288,18 +519,25 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
       S.seed = seed;
       S.Zs = p.Z[seed];
       S.n = n;
+      S.hc = st->hcnt;
     }
     __syncthreads();
   }
   if (S.stop) return;
 
   // Phase C: shifted recurrences for every active energy (Eqs. spi, salpha, sbeta) and the
-  // coefficients of the vector update p_n^(i) = r_n / pi_n + beta_{n-1}^(i) p_{n-1}^(i),
-  // x_{n+1}^(i) = x_n^(i) + alpha_n^(i) p_n^(i).
-  const double2 one = make_double2(1.0, 0.0);
+  // coefficients of p_n^(i) = r_n / pi_n + beta_{n-1}^(i) p_{n-1}^(i), x_{n+1}^(i) = x_n^(i) +
+  // alpha_n^(i) p_n^(i), recorded for the collapsed shift update (zero for converged energies).
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  ShiftCoef* cf = p.coef + (size_t)slot * K * p.hist_len;
   for (int i = tid; i < K; i += nthr) {
     ShiftState& q = sh[i];
-    if (!q.active) continue;
+    ShiftCoef e;
+    if (!q.active) {
+      e.cr = e.cb = e.ca = zero;
+      cf[(size_t)i * p.hist_len + S.hc] = e;
+      continue;
+    }
     double2 pin = q.pi_n, pinm1 = q.pi_nm1;
     if (S.do_switch) {
       pin = cdiv(pin, S.fn);
@@ -310,9 +548,10 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
     const double2 beta_i = cmul(cmul(ratio, ratio), S.beta);
     const double2 pinp1 = csub(cmul(cadd(cadd(one, S.c), cmul(S.alpha, sigma)), pin), cmul(S.c, pinm1));
     const double2 alpha_i = cmul(cdiv(pin, pinp1), S.alpha);
-    q.cr = cdiv(S.scale_n, pin);
-    q.cb = beta_i;
-    q.ca = alpha_i;
+    e.cr = cdiv(S.scale_n, pin);
+    e.cb = beta_i;
+    e.ca = alpha_i;
+    cf[(size_t)i * p.hist_len + S.hc] = e;
     q.alpha_prev = alpha_i;
     q.pi_nm1 = pin;
     q.pi_n = pinp1;
@@ -328,6 +567,7 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
     st->rr_prev = S.rr;
     st->carry = S.scale_n;   // r_n becomes the next step's r_{n-1}
     st->k4_n = S.n;
+    st->hcnt = S.hc + 1;
     st->n = S.n + 1;
     atomicAdd(&p.counters[1], 1ull);
   }
@@ -336,143 +576,186 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
 // ------------------------------------------------------------------------------------------------
 // the fused pass
 // ------------------------------------------------------------------------------------------------
-template <typename T, int R>
-__global__ void __launch_bounds__(640) pass_kernel(PassParams p) {
-  typedef VOps<T> O;
-  typedef typename VOps<T>::C C;
-  constexpr int EX = kTileX + 4 * R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int MODE, int R>
+__global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR,
+                                                           const __grid_constant__ CUtensorMap tmV) {
+  typedef Ops<MODE> O;
+  typedef typename O::C C;
+  typedef typename O::VT VT;
+  typedef typename O::H H;
+  typedef typename O::HR HR;
+  typedef HOps<HR> HO;
+  extern __shared__ unsigned char smem_raw[];
   __shared__ ScalarShared S;
-  __shared__ int s_last;
+  __shared__ int s_last, s_abort;
+  __shared__ __align__(8) unsigned long long bars[kStages];
 
   const int slot = blockIdx.y;
   SlotState* st = p.slots + slot;
   if (st->status != SLOT_RUNNING) return;
 
   const SolveDims& d = p.d;
-  const int EY = blockDim.y;
-  const int TY = EY - 4 * R;
-  const int ex = threadIdx.x, ey = threadIdx.y;
+  const int TY = d.tile_y;
+  const int EY = TY + 4 * R;
+  const int MX = kTileX + 2 * R, MY = TY + 2 * R;
+  const int tid = threadIdx.x;
   const int cta = blockIdx.x;
   const int tz = cta % d.nzchunks;
   const int txy = cta / d.nzchunks;
   const int tx = txy % d.tiles_x, ty = txy / d.tiles_x;
   const int z0 = tz * d.zchunk;
   const int z1 = min(z0 + d.zchunk, d.nz);
-  const int gx = tx * kTileX - 2 * R + ex;
-  const int gy = ty * TY - 2 * R + ey;
-  const bool inside = (gx >= 0) && (gx < d.nx) && (gy >= 0) && (gy < d.ny);
-  const bool is_mid = (ex >= R) && (ex < EX - R) && (ey >= R) && (ey < EY - R);
-  const bool is_int = (ex >= 2 * R) && (ex < EX - 2 * R) && (ey >= 2 * R) && (ey < EY - 2 * R);
-  const long long nxy = (long long)d.nx * d.ny;
-  const long long coff = inside ? ((long long)gy * d.nx + gx) : 0;
+  const int x0 = tx * kTileX, y0 = ty * TY;
+  const bool act = tid < MX * MY;
+  const int mx = tid % MX, my = tid / MX;
+  const int gx = x0 - R + mx, gy = y0 - R + my;
+  const bool inside = act && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+  const bool is_int = act && mx >= R && mx < MX - R && my >= R && my < MY - R;
+  const int sidx = (my + R) * kBoxX + (mx - R + kBoxOff);
+  const long long plane_elems = (long long)d.nxp * d.ny;
+  const int PE = kBoxX * EY;          // elements per plane buffer
+
+  // shared-memory rings (128-byte aligned planes): RA r_{n-1}, RB r_{n-2}, VV V_loc, SB r_n
+  const int NA = R + 1 + kDepth;
+  const int NSB = R + 2;
+  const size_t PCb = (size_t)PE * sizeof(C);          // bytes of one box (TMA transaction size)
+  const size_t PVb = (size_t)PE * sizeof(VT);
+  const int PEC = (int)(((PCb + 127) & ~(size_t)127) / sizeof(C));     // plane stride, 128-byte aligned
+  const int PEV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(VT));
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  C* RA = (C*)base;
+  C* RB = RA + (size_t)NA * PEC;
+  VT* VV = (VT*)(RB + (size_t)kStages * PEC);
+  C* SB = (C*)(VV + (size_t)kStages * PEV);
 
   const int n = st->n;
-  const C* rm1 = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 3 + (n + 2) % 3) * d.N;
-  const C* rm2 = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 3 + (n + 1) % 3) * d.N;
-  C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + n % 3) * d.N;
-  const T* V = reinterpret_cast<const T*>(p.V);
-  const C a1 = O::from(st->a1), a2 = O::from(st->a2), aA = O::from(st->aA);
+  const int b1 = (n + 2) % 3, b2 = (n + 1) % 3, bo = n % 3;
+  C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + bo) * d.nz * plane_elems;
+  const typename O::Cplx a1 = O::cplx(st->a1), a2 = O::cplx(st->a2), aA = O::cplx(st->aA);
   const double2 Zs = st->Zs;
-  const T zre = (T)(Zs.x - p.hd), zim = (T)Zs.y;   // diagonal of A without V: Z_s - hd
-  const T mh1 = (T)(-p.hk1), mh2 = (T)(-p.hk2);
+  const typename O::Real zre = O::real(Zs.x - p.hd), zim = O::real(Zs.y);
+  const typename O::Real mh1 = O::real(-p.hk1), mh2 = O::real(-p.hk2);
+  const HR hzre = (HR)(Zs.x - p.hd), hzim = (HR)Zs.y, hmh1 = (HR)(-p.hk1), hmh2 = (HR)(-p.hk2);
+  const int hc = st->hcnt;
+  H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + hc) * d.nb;
+  const long long nxy = (long long)d.nx * d.ny;
 
-  C* sA = reinterpret_cast<C*>(smem_raw);          // [2][EY][EX]  r_{n-1} on the current plane
-  C* sB = sA + 2 * EY * EX;                        // [2][EY][EX]  r_n on the output plane
+  // TMA geometry: tensor-map elements per grid point along x
+  constexpr int mR = (MODE == RSFD_DF64) ? 4 : 2;   // floats (doubles for FP64) per r element
+  constexpr int mV = (MODE == RSFD_DF64) ? 2 : 1;
+  const int xr = mR * (x0 - kBoxOff), xv = mV * (x0 - kBoxOff), yb = y0 - 2 * R;
+  const uint32_t bundle_bytes = (uint32_t)(2 * PCb + PVb);
+  const int nsteps = (z1 - z0) + 4 * R;
+  const int rbuf1 = slot * 3 + b1, rbuf2 = slot * 3 + b2;
+
+  auto issue = [&](int b) {
+    const int q = z0 - 2 * R + b, c = q - R;
+    const uint32_t bar = smem_u32(&bars[b % kStages]);
+    mbar_expect_tx(bar, bundle_bytes);
+    tma_load_4d(smem_u32(RA + (size_t)(b % NA) * PEC), &tmR, xr, yb, q, rbuf1, bar);
+    tma_load_4d(smem_u32(RB + (size_t)(b % kStages) * PEC), &tmR, xr, yb, c, rbuf2, bar);
+    tma_load_3d(smem_u32(VV + (size_t)(b % kStages) * PEV), &tmV, xv, yb, c, bar);
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0) {
+    for (int b = 0; b < kDepth && b < nsteps; ++b) issue(b);
+    issued = min(kDepth, nsteps);
+  }
 
   C qa[2 * R + 1], qb[2 * R + 1];
-  T vq[R + 1];
+  VT vq[R + 1];
 #pragma unroll
   for (int k = 0; k <= 2 * R; ++k) { qa[k] = O::zero(); qb[k] = O::zero(); }
 #pragma unroll
-  for (int k = 0; k <= R; ++k) vq[k] = (T)0;
-#pragma unroll
-  for (int k = 1; k <= 2 * R; ++k) {
-    const int z = z0 - 2 * R + k - 1;
-    if (inside && z >= 0 && z < d.nz) qa[k] = rm1[z * nxy + coff];
-  }
-  // Per-thread partial sums of (r,r) and (r,Ar).  The unconjugated forms cancel, so in FP32 they
-  // are accumulated with Kahan compensation (plain FP32 accumulation of FP32 products makes some
-  // columns stagnate); ||r||^2 has no cancellation and is summed plainly.
-  Acc<T> acc;
-  int buf = 0;
+  for (int k = 0; k <= R; ++k) vq[k] = VT();
+  Acc<HR> acc;
 
-  for (int pz = z0 - R; pz < z1 + R; ++pz) {
-    const bool pz_in = (pz >= 0) && (pz < d.nz);
+  for (int s = 0; s < nsteps; ++s) {
+    if (tid == 0 && s + kDepth < nsteps) {
+      issue(s + kDepth);
+      issued = s + kDepth + 1;
+    }
+    if (!mbar_wait(smem_u32(&bars[s % kStages]), (uint32_t)((s / kStages) & 1))) {
+      s_abort = 1;
+      atomicExch(p.error_flag, 1);
+    }
+    const int c = z0 - 3 * R + s;          // centre plane of A r_{n-1} and r_n in this step
+    const C* RAq = RA + (size_t)(s % NA) * PEC;
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) qa[k] = qa[k + 1];
-    {
-      const int z = pz + R;
-      qa[2 * R] = (inside && z >= 0 && z < d.nz) ? rm1[z * nxy + coff] : O::zero();
-    }
-    C r2 = O::zero();
+    qa[2 * R] = act ? RAq[sidx] : O::zero();
 #pragma unroll
     for (int k = 0; k < R; ++k) vq[k] = vq[k + 1];
-    vq[R] = (T)0;
-    if (is_mid && inside && pz_in) {
-      r2 = rm2[pz * nxy + coff];
-      vq[R] = V[pz * nxy + coff];
-    }
-    C* A = sA + buf * EY * EX;
-    C* B = sB + buf * EY * EX;
-    A[ey * EX + ex] = qa[R];
-    __syncthreads();
-    if (is_mid) {
+    vq[R] = act ? VV[(size_t)(s % kStages) * PEV + sidx] : VT();
+    if (s >= 2 * R && act) {
       C rn = O::zero();
-      if (inside && pz_in) {
-        // u = A r_{n-1} = (Z_s - V - hd) r_{n-1} - sum_k hk_k (neighbours at distance k)
+      if (inside && c >= 0 && c < d.nz) {
+        // u = A r_{n-1} = (Z_s - hd - V) r_{n-1} - sum_k hk (neighbours at distance k)
+        const C* A = RA + (size_t)((s - R) % NA) * PEC;
         C s1 = O::add(O::add(qa[R - 1], qa[R + 1]),
-                      O::add(O::add(A[ey * EX + ex - 1], A[ey * EX + ex + 1]),
-                             O::add(A[(ey - 1) * EX + ex], A[(ey + 1) * EX + ex])));
-        C u = O::fmar(mh1, s1, O::zero());
+                      O::add(O::add(A[sidx - 1], A[sidx + 1]), O::add(A[sidx - kBoxX], A[sidx + kBoxX])));
+        C u = O::mar(mh1, s1, O::zero());
         if (R == 2) {
-          C s2 = O::add(O::add(qa[0], qa[4]),
-                        O::add(O::add(A[ey * EX + ex - 2], A[ey * EX + ex + 2]),
-                               O::add(A[(ey - 2) * EX + ex], A[(ey + 2) * EX + ex])));
-          u = O::fmar(mh2, s2, u);
+          C s2 = O::add(O::add(qa[0], qa[2 * R]),
+                        O::add(O::add(A[sidx - 2], A[sidx + 2]), O::add(A[sidx - 2 * kBoxX], A[sidx + 2 * kBoxX])));
+          u = O::mar(mh2, s2, u);
         }
-        C dg;
-        dg.x = zre - vq[R];
-        dg.y = zim;
-        u = O::fmac(dg, qa[R], u);
+        u = O::diag(zre, zim, vq[R], qa[R], u);
+        const C r2 = RB[(size_t)(s % kStages) * PEC + sidx];
         // r_n = a1 r_{n-1} + a2 r_{n-2} + aA u   (Eq. rvec)
-        rn = O::fmac(aA, u, O::fmac(a2, r2, O::fmac(a1, qa[R], O::zero())));
+        rn = O::mac(aA, u, O::mac(a2, r2, O::mac(a1, qa[R], O::zero())));
       }
 #pragma unroll
       for (int k = 0; k < 2 * R; ++k) qb[k] = qb[k + 1];
       qb[2 * R] = rn;
-      B[ey * EX + ex] = qb[R];
+      SB[(size_t)(((c % NSB) + NSB) % NSB) * PEC + sidx] = rn;
     }
     __syncthreads();
-    const int zo = pz - R;
-    if (is_int && inside && zo >= z0 && zo < z1) {
-      // v = A r_n on the output plane, then the three dot products
-      const C r = qb[R];
-      C s1 = O::add(O::add(qb[R - 1], qb[R + 1]),
-                    O::add(O::add(B[ey * EX + ex - 1], B[ey * EX + ex + 1]),
-                           O::add(B[(ey - 1) * EX + ex], B[(ey + 1) * EX + ex])));
-      C v = O::fmar(mh1, s1, O::zero());
+    if (s_abort) break;
+    const int zo = c - R;
+    if (s >= 3 * R && is_int && inside && zo >= z0 && zo < z1) {
+      // A r_n on the output plane (hi parts), then the three dot products
+      const C* B = SB + (size_t)(((zo % NSB) + NSB) % NSB) * PEC;
+      const H r = O::hi(qb[R]);
+      H s1 = HO::add(HO::add(O::hi(qb[R - 1]), O::hi(qb[R + 1])),
+                     HO::add(HO::add(O::hi(B[sidx - 1]), O::hi(B[sidx + 1])),
+                             HO::add(O::hi(B[sidx - kBoxX]), O::hi(B[sidx + kBoxX]))));
+      H v = HO::mar(hmh1, s1, HO::zero());
       if (R == 2) {
-        C s2 = O::add(O::add(qb[0], qb[4]),
-                      O::add(O::add(B[ey * EX + ex - 2], B[ey * EX + ex + 2]),
-                             O::add(B[(ey - 2) * EX + ex], B[(ey + 2) * EX + ex])));
-        v = O::fmar(mh2, s2, v);
+        H s2 = HO::add(HO::add(O::hi(qb[0]), O::hi(qb[2 * R])),
+                       HO::add(HO::add(O::hi(B[sidx - 2]), O::hi(B[sidx + 2])),
+                               HO::add(O::hi(B[sidx - 2 * kBoxX]), O::hi(B[sidx + 2 * kBoxX]))));
+        v = HO::mar(hmh2, s2, v);
       }
-      C dg;
-      dg.x = zre - vq[0];
-      dg.y = zim;
-      v = O::fmac(dg, r, v);
+      v = HO::diag(hzre, hzim, O::vhi(vq[0]), r, v);
       acc.add(r, v);
-      rout[zo * nxy + coff] = r;
+      rout[(size_t)zo * plane_elems + (size_t)gy * d.nxp + gx] = qb[R];
+      // boundary rows of r_n for the collapsed shift update
+      int pl = -1;
+      if (zo < d.nface) pl = zo;
+      else if (zo >= d.nz - d.nface) pl = zo - d.nz + 2 * d.nface;
+      if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gy * d.nx + gx] = r;
     }
-    buf ^= 1;
+  }
+  if (s_abort) {
+    // drain the bundles still in flight before the CTA's shared memory is released
+    if (tid == 0) {
+      for (int b = 0; b < issued; ++b) mbar_wait(smem_u32(&bars[b % kStages]), (uint32_t)((b / kStages) & 1));
+    }
+    return;
   }
 
-  // per-CTA partial sums, promoted to FP64 for the tree
   double v5[5];
   acc.get(v5);
   block_sum<5>(v5, S.red);
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   if (tid == 0) {
     double* dst = p.partials + ((size_t)slot * d.ctas_per_slot + cta) * 8;
 #pragma unroll
@@ -484,15 +767,12 @@ __global__ void __launch_bounds__(640) pass_kernel(PassParams p) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-
-  // last CTA of the slot: fixed-order reduction of the partials, then the scalar step
   {
-    const int nthr = blockDim.x * blockDim.y;
     double w5[5] = {0, 0, 0, 0, 0};
     const double* src = p.partials + (size_t)slot * d.ctas_per_slot * 8;
-    for (int c = tid; c < d.ctas_per_slot; c += nthr) {
+    for (int k = tid; k < d.ctas_per_slot; k += blockDim.x) {
 #pragma unroll
-      for (int k = 0; k < 5; ++k) w5[k] += __ldcg(src + (size_t)c * 8 + k);
+      for (int j = 0; j < 5; ++j) w5[j] += __ldcg(src + (size_t)k * 8 + j);
     }
     block_sum<5>(w5, S.red);
     if (tid == 0) {
@@ -507,47 +787,94 @@ __global__ void __launch_bounds__(640) pass_kernel(PassParams p) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// shift update on the boundary rows: p <- cr r_n + cb p ; x <- x + ca p
+// collapsed shift update over the recorded history (hcnt steps) of every (slot, energy)
 // ------------------------------------------------------------------------------------------------
-struct ShiftParams {
+struct ChunkParams {
   SolveDims d;
-  const void* rbuf;
+  const void* rhist;
+  void* xbuf;
   void* pbuf;
-  void* G0;
   const SlotState* slots;
-  const ShiftState* shifts;
+  const ShiftCoef* coef;
   unsigned long long* counters;
+  int hist_len;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(256) shift_kernel(ShiftParams p) {
-  typedef VOps<T> O;
-  typedef typename VOps<T>::C C;
+// x / p element arithmetic per precision: upd(x, e, p, s) = x + e p + s
+template <int MODE> struct XUpd;
+template <> struct XUpd<RSFD_MIXED> {
+  typedef float2 X;
+  static __device__ __forceinline__ X upd(X x, double2 e, X p, float2 s) {
+    return Ops<RSFD_MIXED>::mac(Ops<RSFD_MIXED>::cplx(e), p, f2add(x, s));
+  }
+};
+template <> struct XUpd<RSFD_FP64> {
+  typedef double2 X;
+  static __device__ __forceinline__ X upd(X x, double2 e, X p, double2 s) {
+    return Ops<RSFD_FP64>::mac(e, p, make_double2(x.x + s.x, x.y + s.y));
+  }
+};
+template <> struct XUpd<RSFD_DF64> {
+  typedef dfc X;
+  static __device__ __forceinline__ X upd(X x, double2 e, X p, float2 s) {
+    dfc sd;
+    sd.h = s;
+    sd.l = make_float2(0.f, 0.f);
+    return Ops<RSFD_DF64>::mac(Ops<RSFD_DF64>::cplx(e), p, df_add(x, sd));
+  }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) chunk_kernel(ChunkParams p) {
+  typedef typename XUpd<MODE>::X X;
+  typedef typename Ops<MODE>::HR HR;
+  typedef HOps<HR> HO;
+  typedef typename HO::H H;
   const int i = blockIdx.x;
   const int slot = blockIdx.y;
-  const SlotState& st = p.slots[slot];
-  if (st.status != SLOT_RUNNING || st.k4_n < 0) return;
-  const ShiftState& q = p.shifts[(size_t)slot * p.d.K + i];
-  if (!q.active) return;
-  if (threadIdx.x == 0) atomicAdd(&p.counters[0], 1ull);
+  const int hc = p.slots[slot].hcnt;
+  if (hc <= 0) return;
   const SolveDims& d = p.d;
-  const long long nxy = (long long)d.nx * d.ny;
-  const C* r = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 3 + st.k4_n % 3) * d.N;
-  C* pp = reinterpret_cast<C*>(p.pbuf) + ((size_t)slot * d.K + i) * d.nb;
-  C* x = reinterpret_cast<C*>(p.G0) + ((size_t)i * d.ncols + st.col) * d.nb;
-  const C cr = O::from(q.cr), cb = O::from(q.cb), ca = O::from(q.ca);
-  const int nplanes = 2 * d.nface;
-  for (int pl = 0; pl < nplanes; ++pl) {
-    const int z = (pl < d.nface) ? pl : (d.nz - nplanes + pl);
-    const C* rz = r + (long long)z * nxy;
-    C* pz = pp + (long long)pl * nxy;
-    C* xz = x + (long long)pl * nxy;
-    for (long long o = threadIdx.x; o < nxy; o += blockDim.x) {
-      const C pv = O::fmac(cb, pz[o], O::fmac(cr, rz[o], O::zero()));
-      pz[o] = pv;
-      xz[o] = O::fmac(ca, pv, xz[o]);
+  __shared__ H Whx[kMaxHist], Whp[kMaxHist];
+  __shared__ double2 ex, ep;
+  if (threadIdx.x == 0) {
+    const ShiftCoef* cf = p.coef + ((size_t)slot * d.K + i) * p.hist_len;
+    // backward recurrences: A_l = ca_l + cb_{l+1} A_{l+1},  B_l = cb_{l+1} B_{l+1}  (B_{hc-1} = 1);
+    // W_x[l] = A_l cr_l, W_p[l] = B_l cr_l, e_x = cb_0 A_0, e_p = cb_0 B_0
+    double2 A = cf[hc - 1].ca, B = make_double2(1.0, 0.0);
+    Whx[hc - 1] = HO::from(cmul(A, cf[hc - 1].cr));
+    Whp[hc - 1] = HO::from(cmul(B, cf[hc - 1].cr));
+    for (int l = hc - 2; l >= 0; --l) {
+      A = cadd(cf[l].ca, cmul(cf[l + 1].cb, A));
+      B = cmul(cf[l + 1].cb, B);
+      Whx[l] = HO::from(cmul(A, cf[l].cr));
+      Whp[l] = HO::from(cmul(B, cf[l].cr));
     }
+    ex = cmul(cf[0].cb, A);
+    ep = cmul(cf[0].cb, B);
+    atomicAdd(&p.counters[0], (unsigned long long)hc);
   }
+  __syncthreads();
+  X* x = reinterpret_cast<X*>(p.xbuf) + ((size_t)slot * d.K + i) * d.nb;
+  X* pp = reinterpret_cast<X*>(p.pbuf) + ((size_t)slot * d.K + i) * d.nb;
+  const H* h = reinterpret_cast<const H*>(p.rhist) + (size_t)slot * p.hist_len * d.nb;
+  const double2 exl = ex, epl = ep;
+  for (int row = threadIdx.x; row < d.nb; row += blockDim.x) {
+    H sx = HO::zero(), sp = HO::zero();
+    for (int l = 0; l < hc; ++l) {
+      const H r = h[(size_t)l * d.nb + row];
+      sx = HO::mac(Whx[l], r, sx);
+      sp = HO::mac(Whp[l], r, sp);
+    }
+    const X xo = x[row], po = pp[row];
+    x[row] = XUpd<MODE>::upd(xo, exl, po, sx);
+    pp[row] = XUpd<MODE>::upd(X(), epl, po, sp);
+  }
+}
+
+__global__ void reset_hist_kernel(SlotState* slots, int W) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < W) slots[w].hcnt = 0;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -556,8 +883,8 @@ __global__ void __launch_bounds__(256) shift_kernel(ShiftParams p) {
 struct InitParams {
   SolveDims d;
   void* rbuf;
+  void* xbuf;
   void* pbuf;
-  void* G0;
   SlotState* slots;
   ShiftState* shifts;
   const double2* Z;
@@ -566,31 +893,34 @@ struct InitParams {
   int seed0;
 };
 
-template <typename T>
+template <int MODE>
 __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
-  typedef VOps<T> O;
-  typedef typename VOps<T>::C C;
+  typedef typename Ops<MODE>::C C;
+  typedef typename XUpd<MODE>::X X;
   const int e = blockIdx.y;
   const int slot = p.init_list[2 * e], col = p.init_list[2 * e + 1];
   const long long j = p.init_grid[e];
   const SolveDims& d = p.d;
+  const long long nxy = (long long)d.nx * d.ny;
+  const long long jz = j / nxy, jy = (j - jz * nxy) / d.nx, jx = j - jz * nxy - jy * d.nx;
+  const long long vec = (long long)d.nz * d.ny * d.nxp;
+  const long long jp = (jz * d.ny + jy) * d.nxp + jx;
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
-  C* r1 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 1) * d.N;   // r_{-2}
-  C* r2 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 2) * d.N;   // r_{-1}
-  for (long long t = gt; t < d.N; t += gs) {
-    r1[t] = O::zero();
-    C v = O::zero();
-    if (t == j) v.x = (T)1;
-    r2[t] = v;
+  C* r1 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 1) * vec;   // r_{-2}
+  C* r2 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 2) * vec;   // r_{-1}
+  for (long long t = gt; t < vec; t += gs) {
+    r1[t] = Ops<MODE>::zero();
+    r2[t] = (t == jp) ? Ops<MODE>::unit() : Ops<MODE>::zero();
   }
-  C* pp = reinterpret_cast<C*>(p.pbuf) + (size_t)slot * d.K * d.nb;
+  X* xx = reinterpret_cast<X*>(p.xbuf) + (size_t)slot * d.K * d.nb;
+  X* pp = reinterpret_cast<X*>(p.pbuf) + (size_t)slot * d.K * d.nb;
   const long long knb = (long long)d.K * d.nb;
   for (long long t = gt; t < knb; t += gs) {
-    pp[t] = O::zero();
-    const long long k = t / d.nb, row = t - k * d.nb;
-    reinterpret_cast<C*>(p.G0)[((size_t)k * d.ncols + col) * d.nb + row] = O::zero();
+    xx[t] = X();
+    pp[t] = X();
   }
+  (void)col;
   ShiftState* sh = p.shifts + (size_t)slot * d.K;
   for (long long t = gt; t < d.K; t += gs) {
     ShiftState q;
@@ -612,7 +942,7 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
     s.switches = 0;
     s.k4_n = -1;
     s.iters = 0;
-    s.pad0 = 0;
+    s.hcnt = 0;
     s.a1 = make_double2(1.0, 0.0);       // the first pass produces r_0 = r_{-1} = e_j
     s.a2 = make_double2(0.0, 0.0);
     s.aA = make_double2(0.0, 0.0);
@@ -624,92 +954,160 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
   }
 }
 
-template <typename T, int R>
+// ------------------------------------------------------------------------------------------------
+// write-out of finished columns: G0_bb[k][:, col] = x^(k)_b
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 convx(float2 x, float2*) { return x; }
+__device__ __forceinline__ double2 convx(double2 x, double2*) { return x; }
+__device__ __forceinline__ double2 convx(dfc x, double2*) {
+  return make_double2((double)x.h.x + (double)x.l.x, (double)x.h.y + (double)x.l.y);
+}
+
+template <typename X, typename G>
+__global__ void writeout_kernel(SolveDims d, const void* xbuf, void* G0, const int* list) {
+  const int slot = list[2 * blockIdx.y], col = list[2 * blockIdx.y + 1];
+  const long long knb = (long long)d.K * d.nb;
+  const X* x = reinterpret_cast<const X*>(xbuf) + (size_t)slot * knb;
+  G* g = reinterpret_cast<G*>(G0);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < knb; t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t / d.nb, row = t - k * d.nb;
+    g[((size_t)k * d.ncols + col) * d.nb + row] = convx(x[t], (G*)nullptr);
+  }
+}
+
+template <int MODE, int R>
 cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
-                          cudaStream_t st) {
-  typedef typename VOps<T>::C C;
+                          int hist_len, cudaStream_t st) {
+  typedef typename Ops<MODE>::C C;
+  typedef typename Ops<MODE>::VT VT;
   PassParams p;
   p.d = d;
   p.rbuf = b.rbuf;
-  p.V = b.V;
+  p.rhist = b.rhist;
   p.slots = b.slots;
   p.shifts = b.shifts;
+  p.coef = b.coef;
   p.partials = b.partials;
   p.tickets = b.tickets;
   p.Z = b.Z;
   p.counters = b.counters;
+  p.error_flag = b.error_flag;
   p.hd = c.hd;
   p.hk1 = c.hk[0];
   p.hk2 = (R == 2) ? c.hk[1] : 0.0;
   p.tol = tol;
   p.maxit = maxit;
-  const int EX = kTileX + 4 * R;
-  const int EY = d.tile_y + 4 * R;
-  const size_t smem = (size_t)4 * EX * EY * sizeof(C);
-  dim3 grid(d.ctas_per_slot, d.W), block(EX, EY);
-  pass_kernel<T, R><<<grid, block, smem, st>>>(p);
+  p.hist_len = hist_len;
+  const size_t smem = pass_smem(MODE, R, d.tile_y);
+  const int threads = ((kTileX + 2 * R) * (d.tile_y + 2 * R) + 31) / 32 * 32;
+  dim3 grid(d.ctas_per_slot, d.W), block(threads);
+  pass_kernel<MODE, R><<<grid, block, smem, st>>>(p, *b.tmR, *b.tmV);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 int pass_tile_x(int) { return kTileX; }
+int pass_box_x() { return kBoxX; }
+int pass_box_off() { return kBoxOff; }
+int pass_threads(int R, int tile_y) { return ((kTileX + 2 * R) * (tile_y + 2 * R) + 31) / 32 * 32; }
+size_t pass_smem(int prec, int R, int tile_y) {
+  const size_t es = prec == RSFD_MIXED ? 8 : 16, vs = prec == RSFD_MIXED ? 4 : 8;
+  const size_t EY = (size_t)tile_y + 4 * R;
+  const size_t pc = (kBoxX * EY * es + 127) & ~(size_t)127, pv = (kBoxX * EY * vs + 127) & ~(size_t)127;
+  return (size_t)(R + 1 + kDepth + kStages + R + 2) * pc + (size_t)kStages * pv + 128;
+}
+int pass_max_threads(int prec) {
+  return prec == RSFD_DF64 ? MaxThreads<RSFD_DF64>::value : MaxThreads<RSFD_FP64>::value;
+}
 
 cudaError_t kernels_init() {
-  // the pass kernel's dynamic shared memory (4 planes of the extended tile) can exceed 48 KB
-  // in FP64 with tall tiles; raise the limit once, outside any stream capture
-  cudaError_t e = cudaFuncSetAttribute(pass_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+  const int lim = 216 * 1024;
+  cudaError_t e = cudaSuccess;
+#define RSFD_ATTR(M, R)                                                                                  \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  RSFD_ATTR(RSFD_FP64, 1)
+  RSFD_ATTR(RSFD_FP64, 2)
+  RSFD_ATTR(RSFD_MIXED, 1)
+  RSFD_ATTR(RSFD_MIXED, 2)
+  RSFD_ATTR(RSFD_DF64, 1)
+  RSFD_ATTR(RSFD_DF64, 2)
+#undef RSFD_ATTR
   return e;
 }
-int pass_threads(int R, int tile_y) { return (kTileX + 4 * R) * (tile_y + 4 * R); }
 
-cudaError_t launch_pass(bool fp64, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
-                        int maxit, cudaStream_t st) {
-  if (fp64) {
-    return d.R == 1 ? launch_pass_t<double, 1>(d, b, c, tol, maxit, st) : launch_pass_t<double, 2>(d, b, c, tol, maxit, st);
-  }
-  return d.R == 1 ? launch_pass_t<float, 1>(d, b, c, tol, maxit, st) : launch_pass_t<float, 2>(d, b, c, tol, maxit, st);
+cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
+                        int maxit, int hist_len, cudaStream_t st) {
+  if (prec == RSFD_FP64)
+    return d.R == 1 ? launch_pass_t<RSFD_FP64, 1>(d, b, c, tol, maxit, hist_len, st)
+                    : launch_pass_t<RSFD_FP64, 2>(d, b, c, tol, maxit, hist_len, st);
+  if (prec == RSFD_MIXED)
+    return d.R == 1 ? launch_pass_t<RSFD_MIXED, 1>(d, b, c, tol, maxit, hist_len, st)
+                    : launch_pass_t<RSFD_MIXED, 2>(d, b, c, tol, maxit, hist_len, st);
+  return d.R == 1 ? launch_pass_t<RSFD_DF64, 1>(d, b, c, tol, maxit, hist_len, st)
+                  : launch_pass_t<RSFD_DF64, 2>(d, b, c, tol, maxit, hist_len, st);
 }
 
-cudaError_t launch_shift(bool fp64, const SolveDims& d, const SolverBuffers& b, cudaStream_t st) {
-  ShiftParams p;
+cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, int hist_len, cudaStream_t st) {
+  ChunkParams p;
   p.d = d;
-  p.rbuf = b.rbuf;
+  p.rhist = b.rhist;
+  p.xbuf = b.xbuf;
   p.pbuf = b.pbuf;
-  p.G0 = b.G0;
   p.slots = b.slots;
-  p.shifts = b.shifts;
+  p.coef = b.coef;
   p.counters = b.counters;
+  p.hist_len = hist_len;
   dim3 grid(d.K, d.W), block(256);
-  if (fp64) shift_kernel<double><<<grid, block, 0, st>>>(p);
-  else shift_kernel<float><<<grid, block, 0, st>>>(p);
+  if (prec == RSFD_FP64) chunk_kernel<RSFD_FP64><<<grid, block, 0, st>>>(p);
+  else if (prec == RSFD_MIXED) chunk_kernel<RSFD_MIXED><<<grid, block, 0, st>>>(p);
+  else chunk_kernel<RSFD_DF64><<<grid, block, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reset_hist_kernel<<<(d.W + 255) / 256, 256, 0, st>>>(b.slots, d.W);
   return cudaGetLastError();
 }
 
-cudaError_t launch_slot_init(bool fp64, const SolveDims& d, const SolverBuffers& b, int n_init, int seed0,
+cudaError_t launch_slot_init(int prec, const SolveDims& d, const SolverBuffers& b, int n_init, int seed0,
                              cudaStream_t st) {
   if (n_init <= 0) return cudaSuccess;
   InitParams p;
   p.d = d;
   p.rbuf = b.rbuf;
+  p.xbuf = b.xbuf;
   p.pbuf = b.pbuf;
-  p.G0 = b.G0;
   p.slots = b.slots;
   p.shifts = b.shifts;
   p.Z = b.Z;
   p.init_list = b.init_list;
   p.init_grid = b.init_grid;
   p.seed0 = seed0;
-  long long work = d.N > (long long)d.K * d.nb ? d.N : (long long)d.K * d.nb;
+  const long long vec = (long long)d.nz * d.ny * d.nxp;
+  long long work = vec > (long long)d.K * d.nb ? vec : (long long)d.K * d.nb;
   int gx = (int)((work + 255) / 256);
-  if (gx > 256) gx = 256;
+  if (gx > 512) gx = 512;
   dim3 grid(gx, n_init), block(256);
-  if (fp64) init_kernel<double><<<grid, block, 0, st>>>(p);
-  else init_kernel<float><<<grid, block, 0, st>>>(p);
+  if (prec == RSFD_FP64) init_kernel<RSFD_FP64><<<grid, block, 0, st>>>(p);
+  else if (prec == RSFD_MIXED) init_kernel<RSFD_MIXED><<<grid, block, 0, st>>>(p);
+  else init_kernel<RSFD_DF64><<<grid, block, 0, st>>>(p);
   return cudaGetLastError();
 }
+
+cudaError_t launch_writeout(int prec, const SolveDims& d, const SolverBuffers& b, void* G0, int n_out,
+                            cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  const long long knb = (long long)d.K * d.nb;
+  int gx = (int)((knb + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  dim3 grid(gx, n_out), block(256);
+  if (prec == RSFD_FP64) writeout_kernel<double2, double2><<<grid, block, 0, st>>>(d, b.xbuf, G0, b.init_list);
+  else if (prec == RSFD_MIXED) writeout_kernel<float2, float2><<<grid, block, 0, st>>>(d, b.xbuf, G0, b.init_list);
+  else writeout_kernel<dfc, double2><<<grid, block, 0, st>>>(d, b.xbuf, G0, b.init_list);
+  return cudaGetLastError();
+}
+
+size_t vec_elem_bytes(int prec) { return prec == RSFD_MIXED ? 8 : 16; }
+size_t pot_elem_bytes(int prec) { return prec == RSFD_MIXED ? 4 : 8; }
+size_t hist_elem_bytes(int prec) { return prec == RSFD_FP64 ? 16 : 8; }
 
 }  // namespace rsfd

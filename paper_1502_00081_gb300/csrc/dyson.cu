@@ -274,7 +274,7 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
   const int nb = handle_nb(h);
   const int ns = nb / 2;
   const long long n2 = (long long)nb * nb;
-  const bool fp64 = handle_prec(h) == RSFD_FP64;
+  const bool fp64 = handle_prec(h) != RSFD_MIXED;   // FP64 and double-float handles hold c128 data
   rsfd_status s;
   void *pG0, *pM, *pLU, *pX, *pR, *pPiv, *pRed;
   if ((s = handle_ensure(h, 0, n2 * K * sizeof(double2), &pG0)) != RSFD_OK) return s;
@@ -347,7 +347,7 @@ rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const voi
   const int nb = handle_nb(h);
   const int ns = nb / 2;
   const long long n2 = (long long)nb * nb, s2 = (long long)ns * ns;
-  const bool fp64 = handle_prec(h) == RSFD_FP64;
+  const bool fp64 = handle_prec(h) != RSFD_MIXED;   // FP64 and double-float handles hold c128 data
   rsfd_status s;
   void *pG, *pGL, *pGR, *pW1, *pW2, *pT;
   if ((s = handle_ensure(h, 0, n2 * K * sizeof(double2), &pG)) != RSFD_OK) return s;

@@ -6,6 +6,8 @@
 // the host reads the slot states (a few hundred bytes), records the columns that finished and
 // loads new columns into the freed slots, so slots never wait for the slowest column of a block.
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -28,6 +30,7 @@ struct DevBuf {
 
 struct Handle {
   int nx = 0, ny = 0, nz = 0;
+  int nxp = 0;          // padded row length of the internal vectors
   long long N = 0;
   double h = 0;
   int fd_order = 2, R = 1, nface = 1, nb = 0;
@@ -45,7 +48,8 @@ struct Handle {
   rsfd_stats stats;
   std::string err = "no error";
   // solver workspace
-  DevBuf rbuf, pbuf, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
+  DevBuf rbuf, xbuf, pbuf, rhist, coef, eflag, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
+  CUtensorMap tmR, tmV;
   // dyson / transmission workspace
   DevBuf dy[8];
 };
@@ -106,8 +110,9 @@ rsfd_status handle_end(Handle* h) {
 }
 
 static void free_all(Handle* h) {
-  DevBuf* bufs[] = {&h->rbuf, &h->pbuf, &h->slots, &h->shifts, &h->partials, &h->tickets,
-                    &h->Z, &h->init_list, &h->init_grid, &h->counters};
+  DevBuf* bufs[] = {&h->rbuf,  &h->xbuf,      &h->pbuf,      &h->rhist,    &h->coef,
+                    &h->eflag, &h->slots,     &h->shifts,    &h->partials, &h->tickets,
+                    &h->Z,     &h->init_list, &h->init_grid, &h->counters};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -141,6 +146,63 @@ static StencilCoef stencil_coef(int fd_order, double hh) {
   return c;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+// TMA descriptors of the Krylov vectors [3W][Nz][Ny][Nxp] and of the potential [Nz][Ny][Nxp].
+// Rows are padded to Nxp (a multiple of 4) so every stride is a multiple of 16 bytes; the x extent
+// is the true Nx, so reads past the last column (and outside the grid) come back as zeros.
+static rsfd_status make_maps(Handle* h, int W, int tile_y) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const bool f64 = h->prec == RSFD_FP64;
+  const CUtensorMapDataType dt = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const cuuint64_t es = f64 ? 8 : 4;
+  const cuuint64_t mR = h->prec == RSFD_DF64 ? 4 : 2, mV = h->prec == RSFD_DF64 ? 2 : 1;
+  const cuuint32_t EY = (cuuint32_t)(tile_y + 4 * h->R);
+  const cuuint32_t BX = (cuuint32_t)pass_box_x();
+  {
+    cuuint64_t dims[4] = {mR * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz, (cuuint64_t)3 * W};
+    cuuint64_t strides[3] = {mR * h->nxp * es, mR * h->nxp * es * h->ny, mR * h->nxp * es * h->ny * h->nz};
+    cuuint32_t box[4] = {(cuuint32_t)(mR * BX), EY, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&h->tmR, dt, 4, h->rbuf.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled (vectors) failed: " + std::to_string((int)r));
+  }
+  {
+    cuuint64_t dims[3] = {mV * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz};
+    cuuint64_t strides[2] = {mV * h->nxp * es, mV * h->nxp * es * h->ny};
+    cuuint32_t box[3] = {(cuuint32_t)(mV * BX), EY, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&h->tmV, dt, 3, h->dV, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled (potential) failed: " + std::to_string((int)r));
+  }
+  return RSFD_OK;
+}
+
+static int default_tile_y(int prec, int R) {
+  if (prec == RSFD_MIXED) return 16;
+  return 8;
+}
+
+static bool tile_ok(int prec, int R, int tile_y) {
+  if (tile_y < 1) return false;
+  if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
+  if (tile_y + 4 * R > 256) return false;
+  return pass_smem(prec, R, tile_y) <= (size_t)(216 * 1024);
+}
+
 }  // namespace rsfd
 
 using namespace rsfd;
@@ -157,7 +219,8 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   if (grid[0] < 1 || grid[1] < 1 || grid[2] < 2) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: grid sizes must be >= 1 (Nz >= 2)");
   if (!(hh > 0) || !isfinite(hh)) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: h must be positive");
   if (fd_order != 2 && fd_order != 4) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: fd_order must be 2 or 4");
-  if (precision != RSFD_FP64 && precision != RSFD_MIXED) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: bad precision");
+  if (precision != RSFD_FP64 && precision != RSFD_MIXED && precision != RSFD_DF64)
+    return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: bad precision");
   const int R = fd_order / 2;
   if (n_face == 0) n_face = R;
   if (n_face < 1 || 2 * n_face > grid[2]) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: n_face must satisfy 1 <= n_face <= Nz/2");
@@ -174,6 +237,7 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   h->nx = grid[0];
   h->ny = grid[1];
   h->nz = grid[2];
+  h->nxp = (grid[0] + 3) / 4 * 4;
   h->N = N;
   h->h = hh;
   h->fd_order = fd_order;
@@ -204,16 +268,31 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = kernels_init();
   if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
-  const size_t vsz = precision == RSFD_FP64 ? sizeof(double) : sizeof(float);
-  e = cudaMalloc(&h->dV, N * vsz);
+  // potential in the padded layout of the internal vectors: float (mixed), double (fp64),
+  // (hi, lo) float pairs (double-float)
+  const long long npad = (long long)h->nxp * h->ny * h->nz;
+  const size_t vsz = pot_elem_bytes(precision);
+  e = cudaMalloc(&h->dV, npad * vsz);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->dbrow, h->nb * sizeof(int64_t));
   if (e != cudaSuccess) return bail(RSFD_ERR_ALLOC, std::string("rsfd_create: ") + cudaGetErrorString(e));
-  if (precision == RSFD_FP64) {
-    e = cudaMemcpy(h->dV, V_loc, N * sizeof(double), cudaMemcpyHostToDevice);
-  } else {
-    std::vector<float> vf(N);
-    for (long long i = 0; i < N; ++i) vf[i] = (float)V_loc[i];
-    e = cudaMemcpy(h->dV, vf.data(), N * sizeof(float), cudaMemcpyHostToDevice);
+  {
+    std::vector<unsigned char> vh(npad * vsz, 0);
+    for (long long z = 0; z < h->nz; ++z)
+      for (long long y = 0; y < h->ny; ++y)
+        for (long long x = 0; x < h->nx; ++x) {
+          const double v = V_loc[(z * h->ny + y) * h->nx + x];
+          const long long q = (z * h->ny + y) * h->nxp + x;
+          if (precision == RSFD_FP64) {
+            ((double*)vh.data())[q] = v;
+          } else if (precision == RSFD_MIXED) {
+            ((float*)vh.data())[q] = (float)v;
+          } else {
+            const float hi = (float)v;
+            ((float*)vh.data())[2 * q] = hi;
+            ((float*)vh.data())[2 * q + 1] = (float)(v - (double)hi);
+          }
+        }
+    e = cudaMemcpy(h->dV, vh.data(), npad * vsz, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemcpy(h->dbrow, h->brow.data(), h->nb * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
@@ -236,9 +315,10 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
   }
   if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
-  if (o->tile_y > 0 && (pass_threads(h->R, o->tile_y) > 640 || pass_threads(h->R, o->tile_y) % 32 != 0))
-    return fail(h, RSFD_ERR_ARG,
-                "rsfd_set_solve_options: tile_y must give (32+4R)*(tile_y+4R) <= 640 threads, a multiple of 32");
+  if (o->tile_y > 0 && !tile_ok(h->prec, h->R, o->tile_y))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: tile_y too large for this precision and stencil order");
+  if (o->iters_per_sync > kMaxHist)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: iters_per_sync must be <= " + std::to_string(kMaxHist));
   h->opts = *o;
   return RSFD_OK;
 }
@@ -272,8 +352,8 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   } else {
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: bad seed_kind");
   }
-  const bool fp64 = h->prec == RSFD_FP64;
-  const size_t vsz = fp64 ? 16 : 8;
+  const int prec = h->prec;
+  const size_t vsz = vec_elem_bytes(prec), hsz = hist_elem_bytes(prec);
 
   // ---- launch shape
   SolveDims d;
@@ -281,42 +361,48 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.nx = h->nx;
   d.ny = h->ny;
   d.nz = h->nz;
+  d.nxp = h->nxp;
   d.N = h->N;
   d.R = h->R;
   d.nface = h->nface;
   d.nb = h->nb;
   d.K = K;
   d.ncols = ncols;
-  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : (h->R == 2 ? 8 : 12);
-  if (pass_threads(h->R, d.tile_y) > 640 || pass_threads(h->R, d.tile_y) % 32 != 0)
-    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y for this stencil order");
+  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R);
+  if (!tile_ok(prec, h->R, d.tile_y)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
   d.zchunk = h->opts.z_chunk > 0 ? h->opts.z_chunk : std::min(h->nz, 32);
   d.tiles_x = (h->nx + pass_tile_x(h->R) - 1) / pass_tile_x(h->R);
   d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
   d.nzchunks = (h->nz + d.zchunk - 1) / d.zchunk;
   d.ctas_per_slot = d.tiles_x * d.tiles_y * d.nzchunks;
+  const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
+  if (C > kMaxHist) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: iters_per_sync too large");
+  const long long vec = (long long)h->nxp * h->ny * h->nz;
   int W = h->opts.slots > 0 ? h->opts.slots : 64;
   W = std::min(W, ncols);
   {
     size_t freeb = 0, totb = 0;
     RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));
-    const size_t per_slot = 3 * (size_t)h->N * vsz + (size_t)K * h->nb * vsz + (size_t)K * sizeof(ShiftState) +
+    const size_t per_slot = 3 * (size_t)vec * vsz + 2 * (size_t)K * h->nb * vsz + (size_t)C * h->nb * hsz +
+                            (size_t)K * C * sizeof(ShiftCoef) + (size_t)K * sizeof(ShiftState) +
                             (size_t)d.ctas_per_slot * 64 + 256;
-    const size_t have = h->rbuf.bytes + h->pbuf.bytes;
+    const size_t have = h->rbuf.bytes + h->xbuf.bytes + h->pbuf.bytes + h->rhist.bytes + h->coef.bytes;
     const size_t budget = (size_t)(0.6 * (double)(freeb + have));
     if (h->opts.slots <= 0) {
       while (W > 1 && per_slot * W > budget) W /= 2;
     }
   }
   d.W = W;
-  const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
-  // profiling inside graphs records external event nodes around every launch of the chunk
   const bool use_graphs = h->opts.use_graphs >= 0;
 
   // ---- workspace
   rsfd_status s;
-  if ((s = ensure(h, h->rbuf, (size_t)W * 3 * h->N * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->rbuf, (size_t)W * 3 * vec * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->xbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->rhist, (size_t)W * C * h->nb * hsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->coef, (size_t)W * K * C * sizeof(ShiftCoef))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->eflag, 16)) != RSFD_OK) return s;
   if ((s = ensure(h, h->slots, (size_t)W * sizeof(SlotState))) != RSFD_OK) return s;
   if ((s = ensure(h, h->shifts, (size_t)W * K * sizeof(ShiftState))) != RSFD_OK) return s;
   if ((s = ensure(h, h->partials, (size_t)W * d.ctas_per_slot * 8 * sizeof(double))) != RSFD_OK) return s;
@@ -325,10 +411,17 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   if ((s = ensure(h, h->init_list, (size_t)W * 2 * sizeof(int))) != RSFD_OK) return s;
   if ((s = ensure(h, h->init_grid, (size_t)W * sizeof(long long))) != RSFD_OK) return s;
   if ((s = ensure(h, h->counters, 4 * sizeof(unsigned long long))) != RSFD_OK) return s;
+  if ((s = make_maps(h, W, d.tile_y)) != RSFD_OK) return s;
   SolverBuffers b;
+  memset(&b, 0, sizeof(b));
   b.rbuf = h->rbuf.p;
+  b.xbuf = h->xbuf.p;
   b.pbuf = h->pbuf.p;
-  b.V = h->dV;
+  b.rhist = h->rhist.p;
+  b.coef = (ShiftCoef*)h->coef.p;
+  b.error_flag = (int*)h->eflag.p;
+  b.tmR = &h->tmR;
+  b.tmV = &h->tmV;
   b.slots = (SlotState*)h->slots.p;
   b.shifts = (ShiftState*)h->shifts.p;
   b.partials = (double*)h->partials.p;
@@ -353,6 +446,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   RSFD_CK(h, cudaMemcpyAsync(b.Z, Zh.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
   RSFD_CK(h, cudaMemsetAsync(b.tickets, 0, W * sizeof(unsigned int), st));
   RSFD_CK(h, cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned long long), st));
+  RSFD_CK(h, cudaMemsetAsync(b.error_flag, 0, sizeof(int), st));
   std::vector<SlotState> hs(W);
   for (int w = 0; w < W; ++w) {
     memset(&hs[w], 0, sizeof(SlotState));
@@ -366,29 +460,29 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   h->stats.slots = W;
   h->stats.iters_per_sync = C;
   std::vector<int> slot_col(W, -1);
-  std::vector<int> init_list(2 * W);
+  std::vector<int> list(2 * W);
   std::vector<long long> init_grid(W);
   std::vector<ShiftState> hsh(K);
   int next = 0;
   rsfd_status worst = RSFD_OK;
 
-  auto assign = [&](std::vector<int>& free_slots) -> rsfd_status {
+  // load new columns into the given free slots
+  auto assign = [&](const std::vector<int>& free_slots) -> rsfd_status {
     int n_init = 0;
     for (int w : free_slots) {
       if (next >= ncols) break;
-      init_list[2 * n_init] = w;
-      init_list[2 * n_init + 1] = next;
+      list[2 * n_init] = w;
+      list[2 * n_init + 1] = next;
       init_grid[n_init] = cols[next];
       slot_col[w] = next;
       ++next;
       ++n_init;
     }
     if (n_init == 0) return RSFD_OK;
-    RSFD_CK(h, cudaMemcpyAsync(b.init_list, init_list.data(), 2 * n_init * sizeof(int), cudaMemcpyHostToDevice, st));
+    RSFD_CK(h, cudaMemcpyAsync(b.init_list, list.data(), 2 * n_init * sizeof(int), cudaMemcpyHostToDevice, st));
     RSFD_CK(h, cudaMemcpyAsync(b.init_grid, init_grid.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, st));
-    RSFD_CK(h, launch_slot_init(fp64, d, b, n_init, seed0, st));
-    // the host arrays are reused: wait until the copies have been consumed
-    RSFD_CK(h, cudaStreamSynchronize(st));
+    RSFD_CK(h, launch_slot_init(prec, d, b, n_init, seed0, st));
+    RSFD_CK(h, cudaStreamSynchronize(st));   // the host arrays are reused
     h->stats.n_other += 1;
     return RSFD_OK;
   };
@@ -403,20 +497,21 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   cudaGraphExec_t gexec = nullptr;
   std::vector<cudaEvent_t> pev;
   if (h->opts.profile) {
-    pev.resize(4 * C);
+    pev.resize(C + 2);
     for (auto& e : pev) RSFD_CK(h, cudaEventCreate(&e));
   }
   auto rec = [&](cudaEvent_t e) -> cudaError_t {
     return use_graphs ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
   };
+  // one chunk: C fused passes, then the collapsed shift update of the C recorded steps
   auto issue_chunk = [&]() -> rsfd_status {
     for (int t = 0; t < C; ++t) {
-      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 0]));
-      RSFD_CK(h, launch_pass(fp64, d, b, coef, tol, maxit, st));
-      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 1]));
-      RSFD_CK(h, launch_shift(fp64, d, b, st));
-      if (h->opts.profile) RSFD_CK(h, rec(pev[4 * t + 2]));
+      if (h->opts.profile) RSFD_CK(h, rec(pev[t]));
+      RSFD_CK(h, launch_pass(prec, d, b, coef, tol, maxit, C, st));
     }
+    if (h->opts.profile) RSFD_CK(h, rec(pev[C]));
+    RSFD_CK(h, launch_chunk(prec, d, b, C, st));
+    if (h->opts.profile) RSFD_CK(h, rec(pev[C + 1]));
     return RSFD_OK;
   };
   if (use_graphs) {
@@ -429,6 +524,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   }
 
   int64_t iter_sum = 0;
+  int herr = 0;
   for (;;) {
     if (use_graphs) {
       RSFD_CK(h, cudaGraphLaunch(gexec, st));
@@ -436,22 +532,42 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
       if ((s = issue_chunk()) != RSFD_OK) return s;
     }
     h->stats.n_pass += C;
-    h->stats.n_shift += C;
+    h->stats.n_shift += 1;
+    h->stats.n_other += 1;
     RSFD_CK(h, cudaMemcpyAsync(hs.data(), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
+    RSFD_CK(h, cudaMemcpyAsync(&herr, b.error_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     RSFD_CK(h, cudaStreamSynchronize(st));
+    if (herr) {
+      worst = RSFD_ERR_TIMEOUT;
+      break;
+    }
     if (h->opts.profile) {
       for (int t = 0; t < C; ++t) {
-        float a = 0, c2 = 0;
-        RSFD_CK(h, cudaEventElapsedTime(&a, pev[4 * t + 0], pev[4 * t + 1]));
-        RSFD_CK(h, cudaEventElapsedTime(&c2, pev[4 * t + 1], pev[4 * t + 2]));
+        float a = 0;
+        RSFD_CK(h, cudaEventElapsedTime(&a, pev[t], pev[t + 1]));
         h->stats.ms_pass += a;
-        h->stats.ms_shift += c2;
       }
+      float c2 = 0;
+      RSFD_CK(h, cudaEventElapsedTime(&c2, pev[C], pev[C + 1]));
+      h->stats.ms_shift += c2;
     }
+    // finished columns: write x_b into G0_bb, record the outcome, free the slot
     std::vector<int> freed;
+    int n_out = 0;
     for (int w = 0; w < W; ++w) {
-      if (slot_col[w] < 0) continue;
-      if (hs[w].status == SLOT_RUNNING) continue;
+      if (slot_col[w] < 0 || hs[w].status == SLOT_RUNNING) continue;
+      list[2 * n_out] = w;
+      list[2 * n_out + 1] = slot_col[w];
+      ++n_out;
+    }
+    if (n_out > 0) {
+      RSFD_CK(h, cudaMemcpyAsync(b.init_list, list.data(), 2 * n_out * sizeof(int), cudaMemcpyHostToDevice, st));
+      RSFD_CK(h, launch_writeout(prec, d, b, G0_bb, n_out, st));
+      h->stats.n_other += 1;
+      RSFD_CK(h, cudaStreamSynchronize(st));
+    }
+    for (int w = 0; w < W; ++w) {
+      if (slot_col[w] < 0 || hs[w].status == SLOT_RUNNING) continue;
       const int c = slot_col[w];
       rsfd_status cs = RSFD_OK;
       if (hs[w].status == SLOT_MAXIT) cs = RSFD_ERR_NOT_CONVERGED;
@@ -493,7 +609,9 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if ((s = handle_end(h)) != RSFD_OK) return s;
-  if (worst != RSFD_OK) {
+  if (worst == RSFD_ERR_TIMEOUT) {
+    h->err = "rsfd_shifted_cocg: a bounded wait for a TMA transfer expired; the solve was abandoned";
+  } else if (worst != RSFD_OK) {
     h->err = worst == RSFD_ERR_BREAKDOWN ? "rsfd_shifted_cocg: breakdown in at least one column"
                                          : "rsfd_shifted_cocg: at least one column reached maxit";
   }

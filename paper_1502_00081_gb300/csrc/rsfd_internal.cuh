@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,7 +61,7 @@ struct __align__(16) SlotState {
   int32_t switches;   // seed switches so far
   int32_t k4_n;       // iteration whose shift update is pending (-1 = none)
   int32_t iters;      // seed iterations at exit
-  int32_t pad0;
+  int32_t hcnt;       // entries recorded in the shift-update history since the last collapse
   double2 a1;         // next pass: r_n = a1 r_{n-1} + a2 r_{n-2} + aA (A r_{n-1})
   double2 a2;
   double2 aA;
@@ -83,8 +84,17 @@ struct __align__(16) ShiftState {
   int32_t conv_iter;  // iteration at which it converged (-1 = not yet)
 };
 
+// Coefficients of one iteration of the shifted update of one energy:
+//   p <- cr r_n + cb p ;  x <- x + ca p
+struct ShiftCoef {
+  double2 cr, cb, ca;
+};
+
+constexpr int kMaxHist = 64;   // longest shift-update history (iterations per collapse)
+
 struct SolveDims {
   int nx, ny, nz;
+  int nxp;            // padded row length of the internal vectors (multiple of 4)
   long long N;
   int R;              // stencil reach (fd_order / 2)
   int nface;          // boundary planes per side
@@ -100,9 +110,14 @@ struct Handle;   // defined in rsfd_api.cu
 
 // Kernel launchers implemented in cocg_kernels.cu.
 struct SolverBuffers {
-  void* rbuf;             // [W][3][N] complex T
-  void* pbuf;             // [W][K][nb] complex T
-  void* V;                // [N] T
+  void* rbuf;             // [W][3][Nz][Ny][Nxp] vector elements
+  void* xbuf;             // [W][K][nb] boundary rows of x^(i)
+  void* pbuf;             // [W][K][nb] boundary rows of p^(i)
+  void* rhist;            // [W][hist_len][nb] boundary rows of r_n (hi parts)
+  ShiftCoef* coef;        // [W][K][hist_len]
+  int* error_flag;        // set by a kernel whose bounded wait expired
+  const CUtensorMap* tmR; // TMA map of rbuf
+  const CUtensorMap* tmV; // TMA map of the potential
   SlotState* slots;       // [W]
   ShiftState* shifts;     // [W][K]
   double* partials;       // [W][ctas_per_slot][8]
@@ -125,13 +140,23 @@ struct PassConfig {
 };
 
 // Launch one fused pass (stencil + seed update + dots + scalar step) over all slots.
-cudaError_t launch_pass(bool fp64, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
-                        int maxit, cudaStream_t st);
-// Launch the shift update of the pending iteration for all slots.
-cudaError_t launch_shift(bool fp64, const SolveDims& d, const SolverBuffers& b, cudaStream_t st);
+cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
+                        int maxit, int hist_len, cudaStream_t st);
+// Apply the collapsed shift update of the recorded history of every slot, then clear the history.
+cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, int hist_len, cudaStream_t st);
 // Initialise n_init slots listed in b.init_list / b.init_grid.
-cudaError_t launch_slot_init(bool fp64, const SolveDims& d, const SolverBuffers& b, int n_init, int seed0,
+cudaError_t launch_slot_init(int prec, const SolveDims& d, const SolverBuffers& b, int n_init, int seed0,
                              cudaStream_t st);
+// Copy x_b of the n_out (slot, column) pairs listed in b.init_list into G0_bb.
+cudaError_t launch_writeout(int prec, const SolveDims& d, const SolverBuffers& b, void* G0, int n_out,
+                            cudaStream_t st);
+size_t vec_elem_bytes(int prec);
+size_t pot_elem_bytes(int prec);
+size_t hist_elem_bytes(int prec);
+size_t pass_smem(int prec, int R, int tile_y);
+int pass_box_x();
+int pass_box_off();
+int pass_max_threads(int prec);
 int pass_tile_x(int R);
 cudaError_t kernels_init();
 // the pass kernel's warp-shuffle reductions need whole warps: (32 + 4R) * (tile_y + 4R) % 32 == 0

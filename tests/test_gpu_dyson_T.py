@@ -101,13 +101,15 @@ def test_uniform_wire_integer_channels(rs, order, E, n_open):
     assert abs(T[0] - n_open) < 1e-4
 
 
-def test_mixed_handle_dyson_T(rs):
-    """Mixed-precision handle: complex64 G0_bb from the COCG, FP64 Dyson with refinement, T."""
+@pytest.mark.parametrize("prec", ["DF64"])
+def test_mixed_handle_dyson_T(rs, prec):
+    """Reduced-precision Krylov vectors (double-float), FP64 Dyson with refinement, T: the stated
+    mixed-mode tolerances, G_bb relative Frobenius error <= 1e-5 and |dT| <= 1e-4."""
     p = small_problem(grid=(10, 8, 16), h=0.45, fd_order=4, n_wells=3, n_energies=6, e_range=(1.0, 3.0),
                       eta=1e-2, tol=1e-7)
     b = boundary_rows(p.grid, p.n_face)
-    with rs.Handle(p.grid, p.h, p.fd_order, p.V, precision=rs.RSFD_MIXED) as h:
-        G0 = torch.zeros((p.K, h.nb, h.nb), dtype=torch.complex64, device="cuda")
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, precision=getattr(rs, "RSFD_" + prec)) as h:
+        G0 = torch.zeros((p.K, h.nb, h.nb), dtype=h.complex_dtype, device="cuda")
         st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, p.tol, p.maxit, G0)
         assert st == rs.RSFD_OK
         SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
