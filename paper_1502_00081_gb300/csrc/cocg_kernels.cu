@@ -30,8 +30,8 @@
 //   RSFD_FP64  complex128 vectors, FP64 arithmetic.
 //   RSFD_MIXED complex64 vectors, FP32 arithmetic (packed FFMA2), FP64 scalars and reductions.
 //   RSFD_DF64  complex double-float vectors (hi + lo FP32 pairs, ~48-bit significands) with
-//              error-free FP32 arithmetic and FP64 scalars; the A r_n entering the dot products and
-//              the recorded r_b history use the hi parts.
+//              error-free FP32 arithmetic and FP64 scalars; the recorded r_b history (input of the
+//              collapsed shift update) keeps the hi parts.
 //
 // Every wait in this file is an mbarrier try_wait with an iteration cap; on expiry the CTA raises an
 // error flag that the host turns into RSFD_ERR_TIMEOUT.  No CTA waits on another CTA.
@@ -269,33 +269,49 @@ template <> struct Acc<double> {
   __device__ __forceinline__ void get(double* o) const { o[0] = rr_x; o[1] = rr_y; o[2] = ra_x; o[3] = ra_y; o[4] = nn; }
 };
 
-// The unconjugated forms cancel, so in FP32 they are accumulated with Kahan compensation (plain
-// FP32 accumulation of FP32 products makes some columns stagnate); ||r||^2 has no cancellation.
-template <> struct Acc<float> {
-  float2 rr = make_float2(0.f, 0.f), rr_c = make_float2(0.f, 0.f);
-  float2 ra = make_float2(0.f, 0.f), ra_c = make_float2(0.f, 0.f);
+// FP32-based accumulators (complex64 and double-float vectors).  The unconjugated forms cancel
+// heavily and the COCG scalars are sensitive to them (FP32-rounded products double the iteration
+// count at eta = 1e-3), so every product is formed exactly with an FMA (plus the cross terms of the
+// low parts) and summed into a double-float accumulator with TwoSum.  ||r||^2 has no cancellation
+// and is summed plainly from the leading parts.
+struct AccDF {
+  float2 rr_s = make_float2(0.f, 0.f), rr_l = make_float2(0.f, 0.f);
+  float2 ra_s = make_float2(0.f, 0.f), ra_l = make_float2(0.f, 0.f);
   float nn = 0.f;
-  static __device__ __forceinline__ void kahan(float2& s, float2& c, float2 term) {
-    const float2 y = f2sub(term, c);
-    const float2 t = f2add(s, y);
-    c = f2sub(f2sub(t, s), y);
+  // (s, l) += (a + al) * (b + bl), component-wise, without the al*bl term
+  static __device__ __forceinline__ void addprod(float2& s, float2& l, float2 a, float2 al, float2 b, float2 bl) {
+    const float2 p = f2mul(a, b);
+    float2 e = f2fma(a, b, f2neg(p));
+    e = f2fma(a, bl, e);
+    e = f2fma(al, b, e);
+    float2 t, te;
+    two_sum2(s, p, t, te);
     s = t;
+    l = f2add(l, f2add(te, e));
   }
-  __device__ __forceinline__ void add(float2 r, float2 v) {
-    const float2 trr = make_float2(__fmaf_rn(r.x, r.x, -r.y * r.y), 2.f * r.x * r.y);
-    const float2 tra = make_float2(__fmaf_rn(r.x, v.x, -r.y * v.y), __fmaf_rn(r.x, v.y, r.y * v.x));
-    kahan(rr, rr_c, trr);
-    kahan(ra, ra_c, tra);
-    nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
+  // r*r = (x x - y y, x y + y x);  r*v = (x a - y b, x b + y a)
+  __device__ __forceinline__ void add2(float2 rh, float2 rl, float2 vh, float2 vl) {
+    const float2 xh = bc(rh.x), xl = bc(rl.x);
+    const float2 ny = make_float2(-rh.y, rh.y), nyl = make_float2(-rl.y, rl.y);
+    addprod(rr_s, rr_l, xh, xl, rh, rl);
+    addprod(rr_s, rr_l, ny, nyl, make_float2(rh.y, rh.x), make_float2(rl.y, rl.x));
+    addprod(ra_s, ra_l, xh, xl, vh, vl);
+    addprod(ra_s, ra_l, ny, nyl, make_float2(vh.y, vh.x), make_float2(vl.y, vl.x));
+    nn = __fmaf_rn(rh.x, rh.x, __fmaf_rn(rh.y, rh.y, nn));
   }
+  __device__ __forceinline__ void add(float2 r, float2 v) { add2(r, make_float2(0.f, 0.f), v, make_float2(0.f, 0.f)); }
+  __device__ __forceinline__ void add(const dfc& r, const dfc& v) { add2(r.h, r.l, v.h, v.l); }
   __device__ __forceinline__ void get(double* o) const {
-    o[0] = (double)rr.x - (double)rr_c.x;
-    o[1] = (double)rr.y - (double)rr_c.y;
-    o[2] = (double)ra.x - (double)ra_c.x;
-    o[3] = (double)ra.y - (double)ra_c.y;
+    o[0] = (double)rr_s.x + (double)rr_l.x;
+    o[1] = (double)rr_s.y + (double)rr_l.y;
+    o[2] = (double)ra_s.x + (double)ra_l.x;
+    o[3] = (double)ra_s.y + (double)ra_l.y;
     o[4] = (double)nn;
   }
 };
+
+template <int MODE> struct AccOf { typedef AccDF type; };
+template <> struct AccOf<RSFD_FP64> { typedef Acc<double> type; };
 
 // ------------------------------------------------------------------------------------------------
 // mbarrier / TMA primitives (inline PTX)
@@ -635,7 +651,6 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   const double2 Zs = st->Zs;
   const typename O::Real zre = O::real(Zs.x - p.hd), zim = O::real(Zs.y);
   const typename O::Real mh1 = O::real(-p.hk1), mh2 = O::real(-p.hk2);
-  const HR hzre = (HR)(Zs.x - p.hd), hzim = (HR)Zs.y, hmh1 = (HR)(-p.hk1), hmh2 = (HR)(-p.hk2);
   const int hc = st->hcnt;
   H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + hc) * d.nb;
   const long long nxy = (long long)d.nx * d.ny;
@@ -676,7 +691,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   for (int k = 0; k <= 2 * R; ++k) { qa[k] = O::zero(); qb[k] = O::zero(); }
 #pragma unroll
   for (int k = 0; k <= R; ++k) vq[k] = VT();
-  Acc<HR> acc;
+  typename AccOf<MODE>::type acc;
 
   for (int s = 0; s < nsteps; ++s) {
     if (tid == 0 && s + kDepth < nsteps) {
@@ -722,21 +737,19 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     if (s_abort) break;
     const int zo = c - R;
     if (s >= 3 * R && is_int && inside && zo >= z0 && zo < z1) {
-      // A r_n on the output plane (hi parts), then the three dot products
+      // A r_n on the output plane, then the three dot products
       const C* B = SB + (size_t)(((zo % NSB) + NSB) % NSB) * PEC;
-      const H r = O::hi(qb[R]);
-      H s1 = HO::add(HO::add(O::hi(qb[R - 1]), O::hi(qb[R + 1])),
-                     HO::add(HO::add(O::hi(B[sidx - 1]), O::hi(B[sidx + 1])),
-                             HO::add(O::hi(B[sidx - kBoxX]), O::hi(B[sidx + kBoxX]))));
-      H v = HO::mar(hmh1, s1, HO::zero());
+      C s1 = O::add(O::add(qb[R - 1], qb[R + 1]),
+                    O::add(O::add(B[sidx - 1], B[sidx + 1]), O::add(B[sidx - kBoxX], B[sidx + kBoxX])));
+      C v = O::mar(mh1, s1, O::zero());
       if (R == 2) {
-        H s2 = HO::add(HO::add(O::hi(qb[0]), O::hi(qb[2 * R])),
-                       HO::add(HO::add(O::hi(B[sidx - 2]), O::hi(B[sidx + 2])),
-                               HO::add(O::hi(B[sidx - 2 * kBoxX]), O::hi(B[sidx + 2 * kBoxX]))));
-        v = HO::mar(hmh2, s2, v);
+        C s2 = O::add(O::add(qb[0], qb[2 * R]),
+                      O::add(O::add(B[sidx - 2], B[sidx + 2]), O::add(B[sidx - 2 * kBoxX], B[sidx + 2 * kBoxX])));
+        v = O::mar(mh2, s2, v);
       }
-      v = HO::diag(hzre, hzim, O::vhi(vq[0]), r, v);
-      acc.add(r, v);
+      v = O::diag(zre, zim, vq[0], qb[R], v);
+      acc.add(qb[R], v);
+      const H r = O::hi(qb[R]);
       rout[(size_t)zo * plane_elems + (size_t)gy * d.nxp + gx] = qb[R];
       // boundary rows of r_n for the collapsed shift update
       int pl = -1;
@@ -1018,7 +1031,9 @@ size_t pass_smem(int prec, int R, int tile_y) {
   return (size_t)(R + 1 + kDepth + kStages + R + 2) * pc + (size_t)kStages * pv + 128;
 }
 int pass_max_threads(int prec) {
-  return prec == RSFD_DF64 ? MaxThreads<RSFD_DF64>::value : MaxThreads<RSFD_FP64>::value;
+  if (prec == RSFD_DF64) return MaxThreads<RSFD_DF64>::value;
+  if (prec == RSFD_FP64) return MaxThreads<RSFD_FP64>::value;
+  return MaxThreads<RSFD_MIXED>::value;
 }
 
 cudaError_t kernels_init() {
