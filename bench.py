@@ -212,15 +212,18 @@ def run_gpu(args):
     p = make_problem(args.workload)
     if args.precision:
         p.precision = args.precision
+    if args.maxit:
+        p.maxit = args.maxit
     if args.ncols:
         p.cols = p.cols[:args.ncols]
     cols = rank_columns(p, rank)
     if args.ncols:
         cols = cols[:args.ncols]
-    prec = rs.RSFD_MIXED if p.precision == "mixed" else rs.RSFD_FP64
+    prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[p.precision]
     vsz = 8 if prec == rs.RSFD_MIXED else 16
     h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
-    rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, profile=1)
+    rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, tile_y=args.tile_y,
+                              z_chunk=args.z_chunk, profile=1)
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -238,8 +241,8 @@ def run_gpu(args):
         sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    agg = {"ms_pass": 0.0, "ms_shift": 0.0, "slot_iterations": 0, "shift_updates": 0, "n_pass": 0, "n_shift": 0,
-           "n_other": 0}
+    agg = {"ms_pass": 0.0, "ms_shift": 0.0, "slot_iterations": 0, "shift_updates": 0, "shift_slot_chunks": 0,
+           "n_pass": 0, "n_shift": 0, "n_other": 0}
     statuses, iters = [], []
     for _ in range(args.steps):
         st, info = step()
@@ -260,8 +263,12 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (algorithmic bytes / summed event-timed duration)
     N, nb, K = p.N, h.nb, p.K
-    pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + agg["n_pass"] * 4 * N
-    shift_bytes = agg["shift_updates"] * 4 * vsz * nb + agg["slot_iterations"] * vsz * nb
+    # fused pass: read r_{n-1}, r_{n-2}, write r_n per slot-iteration, plus V once per launch
+    pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + agg["n_pass"] * (vsz // 2) * N
+    # collapsed shift update: read and write x_b, p_b of K energies once per (slot, collapse) and read
+    # the recorded boundary rows of the residuals once
+    hsz = 16 if prec == rs.RSFD_FP64 else 8
+    shift_bytes = agg["shift_slot_chunks"] * K * 4 * vsz * nb + agg["slot_iterations"] * hsz * nb
     peak, peak_src = _peaks()
     kern = {"pass": (pass_bytes, agg["ms_pass"]), "shift": (shift_bytes, agg["ms_shift"])}
     dom = max(kern, key=lambda k: kern[k][1])
@@ -308,7 +315,7 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+f64" if prec == rs.RSFD_MIXED else "c128", "data": "synthetic",
+        "dtype": {rs.RSFD_MIXED: "c64+f64", rs.RSFD_FP64: "c128", rs.RSFD_DF64: "df64(c64x2)+f64"}[prec], "data": "synthetic",
         "config": {"workload": p.name, "grid": list(p.grid), "h": p.h, "fd_order": p.fd_order,
                    "columns_per_gpu": int(cols.size), "energies": K, "eta": p.eta, "tol": p.tol,
                    "precision": p.precision, "boundary_rows": nb, "slots": slots_used,
@@ -367,7 +374,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64", "df64"])
+    ap.add_argument("--maxit", type=int, default=0, help="iteration cap per column (profiling runs)")
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--z-chunk", type=int, default=0)
     ap.add_argument("--ncols", type=int, default=0, help="use only the first n columns (quick runs)")
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--iters-per-sync", type=int, default=0)

@@ -123,6 +123,7 @@ typedef struct {
   int64_t n_other;            /* other kernel launches (slot set-up, reductions) */
   int64_t slot_iterations;    /* sum over columns of seed iterations */
   int64_t shift_updates;      /* recorded (column, energy, iteration) updates applied */
+  int64_t shift_slot_chunks;  /* (column, collapse) pairs: each reads and writes x_b, p_b of K energies once */
   int32_t slots;              /* columns in flight that were used */
   int32_t iters_per_sync;
 } rsfd_stats;

@@ -58,6 +58,7 @@ class rsfd_stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double), ("ms_shift", ctypes.c_double),
                 ("n_pass", ctypes.c_int64), ("n_shift", ctypes.c_int64), ("n_other", ctypes.c_int64),
                 ("slot_iterations", ctypes.c_int64), ("shift_updates", ctypes.c_int64),
+                ("shift_slot_chunks", ctypes.c_int64),
                 ("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32)]
 
 

@@ -55,7 +55,8 @@ constexpr int kStages = kDepth + 1;
 template <int MODE> struct MaxThreads { static constexpr int value = 768; };
 template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 512; };
 template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 512; };
-constexpr long long kWaitCap = 1ll << 22;   // try_wait iterations before a wait is declared lost
+constexpr long long kWaitCap = 1ll << 12;   // try_wait attempts before a wait is declared lost
+constexpr uint32_t kWaitHintNs = 1000000;    // suspend-time hint of one attempt (1 ms): cap ~ 4 s
 
 // ------------------------------------------------------------------------------------------------
 // packed FP32x2 helpers
@@ -324,16 +325,18 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// bounded wait for the phase with the given parity; false when the cap is reached
+// Bounded wait for the phase with the given parity; false when the cap is reached.  Each try_wait
+// carries a suspend-time hint, so a waiting thread sleeps until the phase completes (or the hint
+// expires) instead of spinning through issue slots.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long long i = 0; i < kWaitCap; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     if (ok) return true;
   }
@@ -693,28 +696,33 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   for (int k = 0; k <= R; ++k) vq[k] = VT();
   typename AccOf<MODE>::type acc;
 
+  // ring positions, advanced incrementally: ia = s % NA, ic = (s - R) % NA (valid for s >= R),
+  // ist = s % kStages, par = (s / kStages) & 1, isb = c % NSB, isv = (c - R) % NSB
+  int ia = 0, ic = NA - R, ist = 0, par = 0;
+  int isb = (((z0 - 3 * R) % NSB) + NSB) % NSB;
+  int isv = (((z0 - 4 * R) % NSB) + NSB) % NSB;
   for (int s = 0; s < nsteps; ++s) {
     if (tid == 0 && s + kDepth < nsteps) {
       issue(s + kDepth);
       issued = s + kDepth + 1;
     }
-    if (!mbar_wait(smem_u32(&bars[s % kStages]), (uint32_t)((s / kStages) & 1))) {
+    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
       s_abort = 1;
       atomicExch(p.error_flag, 1);
     }
     const int c = z0 - 3 * R + s;          // centre plane of A r_{n-1} and r_n in this step
-    const C* RAq = RA + (size_t)(s % NA) * PEC;
+    const C* RAq = RA + (size_t)ia * PEC;
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) qa[k] = qa[k + 1];
     qa[2 * R] = act ? RAq[sidx] : O::zero();
 #pragma unroll
     for (int k = 0; k < R; ++k) vq[k] = vq[k + 1];
-    vq[R] = act ? VV[(size_t)(s % kStages) * PEV + sidx] : VT();
+    vq[R] = act ? VV[(size_t)ist * PEV + sidx] : VT();
     if (s >= 2 * R && act) {
       C rn = O::zero();
       if (inside && c >= 0 && c < d.nz) {
         // u = A r_{n-1} = (Z_s - hd - V) r_{n-1} - sum_k hk (neighbours at distance k)
-        const C* A = RA + (size_t)((s - R) % NA) * PEC;
+        const C* A = RA + (size_t)ic * PEC;
         C s1 = O::add(O::add(qa[R - 1], qa[R + 1]),
                       O::add(O::add(A[sidx - 1], A[sidx + 1]), O::add(A[sidx - kBoxX], A[sidx + kBoxX])));
         C u = O::mar(mh1, s1, O::zero());
@@ -724,21 +732,21 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
           u = O::mar(mh2, s2, u);
         }
         u = O::diag(zre, zim, vq[R], qa[R], u);
-        const C r2 = RB[(size_t)(s % kStages) * PEC + sidx];
+        const C r2 = RB[(size_t)ist * PEC + sidx];
         // r_n = a1 r_{n-1} + a2 r_{n-2} + aA u   (Eq. rvec)
         rn = O::mac(aA, u, O::mac(a2, r2, O::mac(a1, qa[R], O::zero())));
       }
 #pragma unroll
       for (int k = 0; k < 2 * R; ++k) qb[k] = qb[k + 1];
       qb[2 * R] = rn;
-      SB[(size_t)(((c % NSB) + NSB) % NSB) * PEC + sidx] = rn;
+      SB[(size_t)isb * PEC + sidx] = rn;
     }
     __syncthreads();
     if (s_abort) break;
     const int zo = c - R;
     if (s >= 3 * R && is_int && inside && zo >= z0 && zo < z1) {
       // A r_n on the output plane, then the three dot products
-      const C* B = SB + (size_t)(((zo % NSB) + NSB) % NSB) * PEC;
+      const C* B = SB + (size_t)isv * PEC;
       C s1 = O::add(O::add(qb[R - 1], qb[R + 1]),
                     O::add(O::add(B[sidx - 1], B[sidx + 1]), O::add(B[sidx - kBoxX], B[sidx + kBoxX])));
       C v = O::mar(mh1, s1, O::zero());
@@ -757,6 +765,11 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       else if (zo >= d.nz - d.nface) pl = zo - d.nz + 2 * d.nface;
       if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gy * d.nx + gx] = r;
     }
+    ia = (ia + 1 == NA) ? 0 : ia + 1;
+    ic = (ic + 1 == NA) ? 0 : ic + 1;
+    if (++ist == kStages) { ist = 0; par ^= 1; }
+    isb = (isb + 1 == NSB) ? 0 : isb + 1;
+    isv = (isv + 1 == NSB) ? 0 : isv + 1;
   }
   if (s_abort) {
     // drain the bundles still in flight before the CTA's shared memory is released
@@ -866,6 +879,7 @@ __global__ void __launch_bounds__(256) chunk_kernel(ChunkParams p) {
     ex = cmul(cf[0].cb, A);
     ep = cmul(cf[0].cb, B);
     atomicAdd(&p.counters[0], (unsigned long long)hc);
+    if (i == 0) atomicAdd(&p.counters[2], 1ull);
   }
   __syncthreads();
   X* x = reinterpret_cast<X*>(p.xbuf) + ((size_t)slot * d.K + i) * d.nb;

@@ -602,6 +602,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   unsigned long long cnt[4];
   RSFD_CK(h, cudaMemcpy(cnt, b.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
   h->stats.shift_updates = (int64_t)cnt[0];
+  h->stats.shift_slot_chunks = (int64_t)cnt[2];
   h->stats.slot_iterations = iter_sum;
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
