@@ -44,6 +44,7 @@
 
 namespace rsfd {
 size_t pass_smem(int prec, int R, int tile_y);
+int pass_threads(int R, int tile_y);
 namespace {
 
 constexpr int kTileX = 32;       // interior tile width in x
@@ -52,9 +53,9 @@ constexpr int kBoxOff = 4;       // the box starts kBoxOff points left of the ti
 constexpr int kDepth = 2;        // bundles (one plane of each input) in flight ahead of the consumers
 constexpr int kStages = kDepth + 1;
 // threads per CTA of the pass kernel (fewer for double-float, which needs more registers per thread)
-template <int MODE> struct MaxThreads { static constexpr int value = 768; };
-template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 512; };
-template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 512; };
+template <int MODE> struct MaxThreads { static constexpr int value = 512; };
+template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 320; };
+template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 320; };
 constexpr long long kWaitCap = 1ll << 12;   // try_wait attempts before a wait is declared lost
 constexpr uint32_t kWaitHintNs = 1000000;    // suspend-time hint of one attempt (1 ms): cap ~ 4 s
 
@@ -221,6 +222,120 @@ template <> struct Ops<RSFD_DF64> {
     r.im = to_dfr(z.y);
     return r;
   }
+};
+
+
+// Unnormalised double-float accumulator: value = s + lo.  Adding a double-float or an exact
+// product costs one TwoSum on the leading parts plus plain additions of the error terms; the pair
+// is renormalised once (FastTwoSum) when the sum is complete.
+struct DFAcc {
+  float2 s, lo;
+};
+__device__ __forceinline__ DFAcc dfacc_zero() {
+  DFAcc a;
+  a.s = make_float2(0.f, 0.f);
+  a.lo = a.s;
+  return a;
+}
+__device__ __forceinline__ DFAcc dfacc_from(const dfc& x) {
+  DFAcc a;
+  a.s = x.h;
+  a.lo = x.l;
+  return a;
+}
+__device__ __forceinline__ void dfacc_add(DFAcc& a, const dfc& x) {
+  float2 t, e;
+  two_sum2(a.s, x.h, t, e);
+  a.s = t;
+  a.lo = f2add(a.lo, f2add(e, x.l));
+}
+// a += c x for a real double-float c (both components), exact leading product via FMA
+__device__ __forceinline__ void dfacc_mul(DFAcc& a, dfr c, const dfc& x) {
+  const float2 ch = bc(c.h);
+  const float2 p = f2mul(ch, x.h);
+  float2 e = f2fma(ch, x.h, f2neg(p));
+  e = f2fma(ch, x.l, e);
+  e = f2fma(bc(c.l), x.h, e);
+  float2 t, te;
+  two_sum2(a.s, p, t, te);
+  a.s = t;
+  a.lo = f2add(a.lo, f2add(te, e));
+}
+__device__ __forceinline__ dfc dfacc_get(const DFAcc& a) {
+  dfc r;
+  fast_two_sum2(a.s, a.lo, r.h, r.l);
+  return r;
+}
+
+// A x at one point: (zre - v + i zim) x - hk1 (sum of the 6 neighbours at distance 1)
+//                                       - hk2 (sum of the 6 neighbours at distance 2)
+// and the seed-residual combination a1 r1 + a2 r2 + aA u, per precision.
+template <int MODE, int R> struct Stencil;
+
+template <int R> struct Stencil<RSFD_MIXED, R> {
+  typedef Ops<RSFD_MIXED> O;
+  static __device__ __forceinline__ float2 sum6(const float2 (&n)[6]) {
+    return f2add(f2add(f2add(n[0], n[1]), f2add(n[2], n[3])), f2add(n[4], n[5]));
+  }
+  static __device__ __forceinline__ float2 applyA(float2 c, const float2 (&n1)[6], const float2 (&n2)[6], float v,
+                                                  float zre, float zim, float mh1, float mh2) {
+    float2 u = f2mul(bc(mh1), sum6(n1));
+    if (R == 2) u = f2fma(bc(mh2), sum6(n2), u);
+    return O::diag(zre, zim, v, c, u);
+  }
+  static __device__ __forceinline__ float2 combine(float2 a1, float2 r1, float2 a2, float2 r2, float2 aA, float2 u) {
+    return O::mac(aA, u, O::mac(a2, r2, O::mac(a1, r1, O::zero())));
+  }
+};
+
+template <int R> struct Stencil<RSFD_FP64, R> {
+  typedef Ops<RSFD_FP64> O;
+  static __device__ __forceinline__ double2 sum6(const double2 (&n)[6]) {
+    return O::add(O::add(O::add(n[0], n[1]), O::add(n[2], n[3])), O::add(n[4], n[5]));
+  }
+  static __device__ __forceinline__ double2 applyA(double2 c, const double2 (&n1)[6], const double2 (&n2)[6],
+                                                   double v, double zre, double zim, double mh1, double mh2) {
+    double2 u = O::mar(mh1, sum6(n1), O::zero());
+    if (R == 2) u = O::mar(mh2, sum6(n2), u);
+    return O::diag(zre, zim, v, c, u);
+  }
+  static __device__ __forceinline__ double2 combine(double2 a1, double2 r1, double2 a2, double2 r2, double2 aA,
+                                                    double2 u) {
+    return O::mac(aA, u, O::mac(a2, r2, O::mac(a1, r1, O::zero())));
+  }
+};
+
+template <int R> struct Stencil<RSFD_DF64, R> {
+  static __device__ __forceinline__ dfc sum6(const dfc (&n)[6]) {
+    DFAcc a = dfacc_from(n[0]);
+#pragma unroll
+    for (int k = 1; k < 6; ++k) dfacc_add(a, n[k]);
+    return dfacc_get(a);
+  }
+  static __device__ __forceinline__ dfc applyA(const dfc& c, const dfc (&n1)[6], const dfc (&n2)[6], float2 v,
+                                               dfr zre, dfr zim, dfr mh1, dfr mh2) {
+    DFAcc a = dfacc_zero();
+    dfacc_mul(a, mh1, sum6(n1));
+    if (R == 2) dfacc_mul(a, mh2, sum6(n2));
+    dfacc_mul(a, dfr_sub(zre, v.x, v.y), c);
+    dfacc_mul(a, zim, df_swapneg(c));
+    return dfacc_get(a);
+  }
+  static __device__ __forceinline__ dfc combine(const dfz& a1, const dfc& r1, const dfz& a2, const dfc& r2,
+                                                const dfz& aA, const dfc& u) {
+    DFAcc a = dfacc_zero();
+    dfacc_mul(a, a1.re, r1);
+    dfacc_mul(a, a1.im, df_swapneg(r1));
+    dfacc_mul(a, a2.re, r2);
+    dfacc_mul(a, a2.im, df_swapneg(r2));
+    dfacc_mul(a, aA.re, u);
+    dfacc_mul(a, aA.im, df_swapneg(u));
+    return dfacc_get(a);
+  }
+};
+
+template <class T> struct Pair {
+  T a, b;
 };
 
 // arithmetic on the "hi" element H (A r_n for the dot products, history, collapsed update)
@@ -599,11 +714,12 @@ template <int MODE, int R>
 __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR,
                                                            const __grid_constant__ CUtensorMap tmV) {
   typedef Ops<MODE> O;
+  typedef Stencil<MODE, R> ST;
   typedef typename O::C C;
   typedef typename O::VT VT;
   typedef typename O::H H;
-  typedef typename O::HR HR;
-  typedef HOps<HR> HO;
+  typedef Pair<C> PC;
+  typedef Pair<VT> PV;
   extern __shared__ unsigned char smem_raw[];
   __shared__ ScalarShared S;
   __shared__ int s_last, s_abort;
@@ -613,10 +729,15 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   SlotState* st = p.slots + slot;
   if (st->status != SLOT_RUNNING) return;
 
+  // Each thread owns two x-adjacent grid points ("a pair").  Pairs of the middle region cover
+  // x in [x0 - 2, x0 + 34) (18 pairs) and y in [y0 - R, y0 + TY + R); the tile proper is pairs
+  // 1..16 and rows R..MY-R-1.
   const SolveDims& d = p.d;
   const int TY = d.tile_y;
   const int EY = TY + 4 * R;
-  const int MX = kTileX + 2 * R, MY = TY + 2 * R;
+  constexpr int MXP = 18;              // pairs per middle row
+  constexpr int BXP = kBoxX / 2;       // pairs per box row (20)
+  const int MY = TY + 2 * R;
   const int tid = threadIdx.x;
   const int cta = blockIdx.x;
   const int tz = cta % d.nzchunks;
@@ -625,27 +746,28 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   const int z0 = tz * d.zchunk;
   const int z1 = min(z0 + d.zchunk, d.nz);
   const int x0 = tx * kTileX, y0 = ty * TY;
-  const bool act = tid < MX * MY;
-  const int mx = tid % MX, my = tid / MX;
-  const int gx = x0 - R + mx, gy = y0 - R + my;
-  const bool inside = act && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-  const bool is_int = act && mx >= R && mx < MX - R && my >= R && my < MY - R;
-  const int sidx = (my + R) * kBoxX + (mx - R + kBoxOff);
+  const bool act = tid < MXP * MY;
+  const int px = tid % MXP, my = tid / MXP;
+  const int gxa = x0 - 2 + 2 * px, gy = y0 - R + my;
+  const bool yin = act && gy >= 0 && gy < d.ny;
+  const bool ina = yin && gxa >= 0 && gxa < d.nx;
+  const bool inb = yin && gxa + 1 >= 0 && gxa + 1 < d.nx;
+  const bool is_int = act && px >= 1 && px < MXP - 1 && my >= R && my < MY - R;
+  const int sidx = (my + R) * BXP + (px + 1);
   const long long plane_elems = (long long)d.nxp * d.ny;
-  const int PE = kBoxX * EY;          // elements per plane buffer
 
   // shared-memory rings (128-byte aligned planes): RA r_{n-1}, RB r_{n-2}, VV V_loc, SB r_n
   const int NA = R + 1 + kDepth;
   const int NSB = R + 2;
-  const size_t PCb = (size_t)PE * sizeof(C);          // bytes of one box (TMA transaction size)
-  const size_t PVb = (size_t)PE * sizeof(VT);
-  const int PEC = (int)(((PCb + 127) & ~(size_t)127) / sizeof(C));     // plane stride, 128-byte aligned
-  const int PEV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(VT));
+  const size_t PCb = (size_t)kBoxX * EY * sizeof(C);          // bytes of one box (TMA transaction size)
+  const size_t PVb = (size_t)kBoxX * EY * sizeof(VT);
+  const int PEC = (int)(((PCb + 127) & ~(size_t)127) / sizeof(PC));    // plane stride in pairs
+  const int PEV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(PV));
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  C* RA = (C*)base;
-  C* RB = RA + (size_t)NA * PEC;
-  VT* VV = (VT*)(RB + (size_t)kStages * PEC);
-  C* SB = (C*)(VV + (size_t)kStages * PEV);
+  PC* RA = (PC*)base;
+  PC* RB = RA + (size_t)NA * PEC;
+  PV* VV = (PV*)(RB + (size_t)kStages * PEC);
+  PC* SB = (PC*)(VV + (size_t)kStages * PEV);
 
   const int n = st->n;
   const int b1 = (n + 2) % 3, b2 = (n + 1) % 3, bo = n % 3;
@@ -666,13 +788,13 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   const int nsteps = (z1 - z0) + 4 * R;
   const int rbuf1 = slot * 3 + b1, rbuf2 = slot * 3 + b2;
 
-  auto issue = [&](int b) {
-    const int q = z0 - 2 * R + b, c = q - R;
-    const uint32_t bar = smem_u32(&bars[b % kStages]);
+  auto issue = [&](int bnd) {
+    const int q = z0 - 2 * R + bnd, c = q - R;
+    const uint32_t bar = smem_u32(&bars[bnd % kStages]);
     mbar_expect_tx(bar, bundle_bytes);
-    tma_load_4d(smem_u32(RA + (size_t)(b % NA) * PEC), &tmR, xr, yb, q, rbuf1, bar);
-    tma_load_4d(smem_u32(RB + (size_t)(b % kStages) * PEC), &tmR, xr, yb, c, rbuf2, bar);
-    tma_load_3d(smem_u32(VV + (size_t)(b % kStages) * PEV), &tmV, xv, yb, c, bar);
+    tma_load_4d(smem_u32(RA + (size_t)(bnd % NA) * PEC), &tmR, xr, yb, q, rbuf1, bar);
+    tma_load_4d(smem_u32(RB + (size_t)(bnd % kStages) * PEC), &tmR, xr, yb, c, rbuf2, bar);
+    tma_load_3d(smem_u32(VV + (size_t)(bnd % kStages) * PEV), &tmV, xv, yb, c, bar);
   };
 
   if (tid == 0) {
@@ -684,23 +806,27 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   __syncthreads();
   int issued = 0;
   if (tid == 0) {
-    for (int b = 0; b < kDepth && b < nsteps; ++b) issue(b);
+    for (int bnd = 0; bnd < kDepth && bnd < nsteps; ++bnd) issue(bnd);
     issued = min(kDepth, nsteps);
   }
 
-  C qa[2 * R + 1], qb[2 * R + 1];
-  VT vq[R + 1];
+  // z-queues of this thread's pair: r_{n-1} on planes c-R..c+R, r_n on planes c-2R..c, V on c-2R..c
+  PC qa[2 * R + 1], qb[2 * R + 1];
+  PV vq[2 * R + 1];
+  const C zc = O::zero();
 #pragma unroll
-  for (int k = 0; k <= 2 * R; ++k) { qa[k] = O::zero(); qb[k] = O::zero(); }
-#pragma unroll
-  for (int k = 0; k <= R; ++k) vq[k] = VT();
+  for (int k = 0; k <= 2 * R; ++k) {
+    qa[k].a = zc; qa[k].b = zc;
+    qb[k].a = zc; qb[k].b = zc;
+    vq[k].a = VT(); vq[k].b = VT();
+  }
   typename AccOf<MODE>::type acc;
-
-  // ring positions, advanced incrementally: ia = s % NA, ic = (s - R) % NA (valid for s >= R),
-  // ist = s % kStages, par = (s / kStages) & 1, isb = c % NSB, isv = (c - R) % NSB
+  // ring positions, advanced incrementally: ia = s % NA, ic = (s - R) % NA, ist = s % kStages,
+  // par = (s / kStages) & 1, isb = c % NSB, isv = (c - R) % NSB
   int ia = 0, ic = NA - R, ist = 0, par = 0;
   int isb = (((z0 - 3 * R) % NSB) + NSB) % NSB;
   int isv = (((z0 - 4 * R) % NSB) + NSB) % NSB;
+
   for (int s = 0; s < nsteps; ++s) {
     if (tid == 0 && s + kDepth < nsteps) {
       issue(s + kDepth);
@@ -711,30 +837,41 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       atomicExch(p.error_flag, 1);
     }
     const int c = z0 - 3 * R + s;          // centre plane of A r_{n-1} and r_n in this step
-    const C* RAq = RA + (size_t)ia * PEC;
 #pragma unroll
-    for (int k = 0; k < 2 * R; ++k) qa[k] = qa[k + 1];
-    qa[2 * R] = act ? RAq[sidx] : O::zero();
-#pragma unroll
-    for (int k = 0; k < R; ++k) vq[k] = vq[k + 1];
-    vq[R] = act ? VV[(size_t)ist * PEV + sidx] : VT();
+    for (int k = 0; k < 2 * R; ++k) { qa[k] = qa[k + 1]; vq[k] = vq[k + 1]; }
+    if (act) {
+      qa[2 * R] = RA[(size_t)ia * PEC + sidx];
+      vq[2 * R] = VV[(size_t)ist * PEV + sidx];
+    }
     if (s >= 2 * R && act) {
-      C rn = O::zero();
-      if (inside && c >= 0 && c < d.nz) {
-        // u = A r_{n-1} = (Z_s - hd - V) r_{n-1} - sum_k hk (neighbours at distance k)
-        const C* A = RA + (size_t)ic * PEC;
-        C s1 = O::add(O::add(qa[R - 1], qa[R + 1]),
-                      O::add(O::add(A[sidx - 1], A[sidx + 1]), O::add(A[sidx - kBoxX], A[sidx + kBoxX])));
-        C u = O::mar(mh1, s1, O::zero());
-        if (R == 2) {
-          C s2 = O::add(O::add(qa[0], qa[2 * R]),
-                        O::add(O::add(A[sidx - 2], A[sidx + 2]), O::add(A[sidx - 2 * kBoxX], A[sidx + 2 * kBoxX])));
-          u = O::mar(mh2, s2, u);
-        }
-        u = O::diag(zre, zim, vq[R], qa[R], u);
-        const C r2 = RB[(size_t)ist * PEC + sidx];
-        // r_n = a1 r_{n-1} + a2 r_{n-2} + aA u   (Eq. rvec)
-        rn = O::mac(aA, u, O::mac(a2, r2, O::mac(a1, qa[R], O::zero())));
+      const PC* A = RA + (size_t)ic * PEC;
+      const PC L = A[sidx - 1], Rt = A[sidx + 1], U1 = A[sidx - BXP], D1 = A[sidx + BXP];
+      PC U2, D2;
+      if (R == 2) { U2 = A[sidx - 2 * BXP]; D2 = A[sidx + 2 * BXP]; } else { U2.a = U2.b = D2.a = D2.b = zc; }
+      const PC r2 = RB[(size_t)ist * PEC + sidx];
+      const PC cq = qa[R];
+      // u = A r_{n-1} at both points of the pair
+      const C n1a[6] = {qa[R - 1].a, qa[R + 1].a, L.b, cq.b, U1.a, D1.a};
+      const C n1b[6] = {qa[R - 1].b, qa[R + 1].b, cq.a, Rt.a, U1.b, D1.b};
+      C n2a[6], n2b[6];
+      if (R == 2) {
+        n2a[0] = qa[0].a; n2a[1] = qa[2 * R].a; n2a[2] = L.a; n2a[3] = Rt.a; n2a[4] = U2.a; n2a[5] = D2.a;
+        n2b[0] = qa[0].b; n2b[1] = qa[2 * R].b; n2b[2] = L.b; n2b[3] = Rt.b; n2b[4] = U2.b; n2b[5] = D2.b;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { n2a[k] = zc; n2b[k] = zc; }
+      }
+      const bool cin = c >= 0 && c < d.nz;
+      PC rn;
+      rn.a = zc;
+      rn.b = zc;
+      if (cin && ina) {
+        const C u = ST::applyA(cq.a, n1a, n2a, vq[2 * R].a, zre, zim, mh1, mh2);
+        rn.a = ST::combine(a1, cq.a, a2, r2.a, aA, u);          // Eq. rvec
+      }
+      if (cin && inb) {
+        const C u = ST::applyA(cq.b, n1b, n2b, vq[2 * R].b, zre, zim, mh1, mh2);
+        rn.b = ST::combine(a1, cq.b, a2, r2.b, aA, u);
       }
 #pragma unroll
       for (int k = 0; k < 2 * R; ++k) qb[k] = qb[k + 1];
@@ -744,26 +881,39 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     __syncthreads();
     if (s_abort) break;
     const int zo = c - R;
-    if (s >= 3 * R && is_int && inside && zo >= z0 && zo < z1) {
+    if (s >= 3 * R && is_int && yin && zo >= z0 && zo < z1 && ina) {
       // A r_n on the output plane, then the three dot products
-      const C* B = SB + (size_t)isv * PEC;
-      C s1 = O::add(O::add(qb[R - 1], qb[R + 1]),
-                    O::add(O::add(B[sidx - 1], B[sidx + 1]), O::add(B[sidx - kBoxX], B[sidx + kBoxX])));
-      C v = O::mar(mh1, s1, O::zero());
+      const PC* B = SB + (size_t)isv * PEC;
+      const PC L = B[sidx - 1], Rt = B[sidx + 1], U1 = B[sidx - BXP], D1 = B[sidx + BXP];
+      PC U2, D2;
+      if (R == 2) { U2 = B[sidx - 2 * BXP]; D2 = B[sidx + 2 * BXP]; } else { U2.a = U2.b = D2.a = D2.b = zc; }
+      const PC cq = qb[R];
+      const C n1a[6] = {qb[R - 1].a, qb[R + 1].a, L.b, cq.b, U1.a, D1.a};
+      const C n1b[6] = {qb[R - 1].b, qb[R + 1].b, cq.a, Rt.a, U1.b, D1.b};
+      C n2a[6], n2b[6];
       if (R == 2) {
-        C s2 = O::add(O::add(qb[0], qb[2 * R]),
-                      O::add(O::add(B[sidx - 2], B[sidx + 2]), O::add(B[sidx - 2 * kBoxX], B[sidx + 2 * kBoxX])));
-        v = O::mar(mh2, s2, v);
+        n2a[0] = qb[0].a; n2a[1] = qb[2 * R].a; n2a[2] = L.a; n2a[3] = Rt.a; n2a[4] = U2.a; n2a[5] = D2.a;
+        n2b[0] = qb[0].b; n2b[1] = qb[2 * R].b; n2b[2] = L.b; n2b[3] = Rt.b; n2b[4] = U2.b; n2b[5] = D2.b;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { n2a[k] = zc; n2b[k] = zc; }
       }
-      v = O::diag(zre, zim, vq[0], qb[R], v);
-      acc.add(qb[R], v);
-      const H r = O::hi(qb[R]);
-      rout[(size_t)zo * plane_elems + (size_t)gy * d.nxp + gx] = qb[R];
-      // boundary rows of r_n for the collapsed shift update
+      const C va = ST::applyA(cq.a, n1a, n2a, vq[R].a, zre, zim, mh1, mh2);
+      acc.add(cq.a, va);
+      C* dst = rout + (size_t)zo * plane_elems + (size_t)gy * d.nxp + gxa;
       int pl = -1;
       if (zo < d.nface) pl = zo;
       else if (zo >= d.nz - d.nface) pl = zo - d.nz + 2 * d.nface;
-      if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gy * d.nx + gx] = r;
+      H* hrow = hist + (size_t)pl * nxy + (size_t)gy * d.nx + gxa;
+      if (inb) {
+        const C vb = ST::applyA(cq.b, n1b, n2b, vq[R].b, zre, zim, mh1, mh2);
+        acc.add(cq.b, vb);
+        *reinterpret_cast<PC*>(dst) = cq;
+        if (pl >= 0) { hrow[0] = O::hi(cq.a); hrow[1] = O::hi(cq.b); }
+      } else {
+        dst[0] = cq.a;
+        if (pl >= 0) hrow[0] = O::hi(cq.a);
+      }
     }
     ia = (ia + 1 == NA) ? 0 : ia + 1;
     ic = (ic + 1 == NA) ? 0 : ic + 1;
@@ -774,7 +924,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   if (s_abort) {
     // drain the bundles still in flight before the CTA's shared memory is released
     if (tid == 0) {
-      for (int b = 0; b < issued; ++b) mbar_wait(smem_u32(&bars[b % kStages]), (uint32_t)((b / kStages) & 1));
+      for (int bnd = 0; bnd < issued; ++bnd) mbar_wait(smem_u32(&bars[bnd % kStages]), (uint32_t)((bnd / kStages) & 1));
     }
     return;
   }
@@ -1026,7 +1176,7 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.maxit = maxit;
   p.hist_len = hist_len;
   const size_t smem = pass_smem(MODE, R, d.tile_y);
-  const int threads = ((kTileX + 2 * R) * (d.tile_y + 2 * R) + 31) / 32 * 32;
+  const int threads = pass_threads(R, d.tile_y);
   dim3 grid(d.ctas_per_slot, d.W), block(threads);
   pass_kernel<MODE, R><<<grid, block, smem, st>>>(p, *b.tmR, *b.tmV);
   return cudaGetLastError();
@@ -1037,7 +1187,7 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
 int pass_tile_x(int) { return kTileX; }
 int pass_box_x() { return kBoxX; }
 int pass_box_off() { return kBoxOff; }
-int pass_threads(int R, int tile_y) { return ((kTileX + 2 * R) * (tile_y + 2 * R) + 31) / 32 * 32; }
+int pass_threads(int R, int tile_y) { return (18 * (tile_y + 2 * R) + 31) / 32 * 32; }
 size_t pass_smem(int prec, int R, int tile_y) {
   const size_t es = prec == RSFD_MIXED ? 8 : 16, vs = prec == RSFD_MIXED ? 4 : 8;
   const size_t EY = (size_t)tile_y + 4 * R;

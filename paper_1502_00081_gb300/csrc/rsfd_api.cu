@@ -192,8 +192,8 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y) {
 }
 
 static int default_tile_y(int prec, int R) {
-  if (prec == RSFD_MIXED) return 16;
-  return 8;
+  if (prec == RSFD_MIXED) return 24;
+  return 12;
 }
 
 static bool tile_ok(int prec, int R, int tile_y) {
