@@ -62,9 +62,11 @@ constexpr uint32_t kWaitHintNs = 1000000;    // suspend-time hint of one attempt
 // ------------------------------------------------------------------------------------------------
 // packed FP32x2 helpers
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+// Packed adds and subtracts are written as FFMA2 with a +-1 multiplier: one issued instruction and
+// the same single rounding as an add (the packed add instruction costs about two issue slots here).
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __ffma2_rn(a, make_float2(1.f, 1.f), b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
@@ -251,15 +253,16 @@ __device__ __forceinline__ void dfacc_add(DFAcc& a, const dfc& x) {
 }
 // a += c x for a real double-float c (both components), exact leading product via FMA
 __device__ __forceinline__ void dfacc_mul(DFAcc& a, dfr c, const dfc& x) {
-  const float2 ch = bc(c.h);
-  const float2 p = f2mul(ch, x.h);
-  float2 e = f2fma(ch, x.h, f2neg(p));
-  e = f2fma(ch, x.l, e);
-  e = f2fma(bc(c.l), x.h, e);
+  // ne = p - c x (exact leading part, then the low-order terms), accumulated with the opposite sign
+  const float2 nch = bc(-c.h);
+  const float2 p = f2mul(bc(c.h), x.h);
+  float2 ne = f2fma(nch, x.h, p);
+  ne = f2fma(nch, x.l, ne);
+  ne = f2fma(bc(-c.l), x.h, ne);
   float2 t, te;
   two_sum2(a.s, p, t, te);
   a.s = t;
-  a.lo = f2add(a.lo, f2add(te, e));
+  a.lo = f2add(a.lo, f2sub(te, ne));
 }
 __device__ __forceinline__ dfc dfacc_get(const DFAcc& a) {
   dfc r;
@@ -396,14 +399,15 @@ struct AccDF {
   float nn = 0.f;
   // (s, l) += (a + al) * (b + bl), component-wise, without the al*bl term
   static __device__ __forceinline__ void addprod(float2& s, float2& l, float2 a, float2 al, float2 b, float2 bl) {
+    const float2 na = f2neg(a);
     const float2 p = f2mul(a, b);
-    float2 e = f2fma(a, b, f2neg(p));
-    e = f2fma(a, bl, e);
-    e = f2fma(al, b, e);
+    float2 ne = f2fma(na, b, p);          // p - a b, exact
+    ne = f2fma(na, bl, ne);
+    ne = f2fma(f2neg(al), b, ne);
     float2 t, te;
     two_sum2(s, p, t, te);
     s = t;
-    l = f2add(l, f2add(te, e));
+    l = f2add(l, f2sub(te, ne));
   }
   // r*r = (x x - y y, x y + y x);  r*v = (x a - y b, x b + y a)
   __device__ __forceinline__ void add2(float2 rh, float2 rl, float2 vh, float2 vl) {
@@ -417,12 +421,31 @@ struct AccDF {
   }
   __device__ __forceinline__ void add(float2 r, float2 v) { add2(r, make_float2(0.f, 0.f), v, make_float2(0.f, 0.f)); }
   __device__ __forceinline__ void add(const dfc& r, const dfc& v) { add2(r.h, r.l, v.h, v.l); }
-  __device__ __forceinline__ void get(double* o) const {
-    o[0] = (double)rr_s.x + (double)rr_l.x;
-    o[1] = (double)rr_s.y + (double)rr_l.y;
-    o[2] = (double)ra_s.x + (double)ra_l.x;
-    o[3] = (double)ra_s.y + (double)ra_l.y;
-    o[4] = (double)nn;
+  static __device__ __forceinline__ float2 shfl2(float2 v, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+  }
+  static __device__ __forceinline__ void merge(float2& s, float2& l, float2 os, float2 ol) {
+    float2 t, te;
+    two_sum2(s, os, t, te);
+    s = t;
+    l = f2add(l, f2add(te, ol));
+  }
+  // Reduce over the warp in double-float (whole warps only), then convert once per warp: lane 0
+  // returns the warp's sums in FP64, the other lanes zeros.
+  __device__ __forceinline__ void get(double* o) {
+    for (int off = 16; off > 0; off >>= 1) {
+      const float2 a = shfl2(rr_s, off), b = shfl2(rr_l, off), c = shfl2(ra_s, off), d = shfl2(ra_l, off);
+      merge(rr_s, rr_l, a, b);
+      merge(ra_s, ra_l, c, d);
+    }
+    double nnd = (double)nn;
+    for (int off = 16; off > 0; off >>= 1) nnd += __shfl_down_sync(0xffffffffu, nnd, off);
+    const bool lead = (threadIdx.x & 31) == 0;
+    o[0] = lead ? (double)rr_s.x + (double)rr_l.x : 0.0;
+    o[1] = lead ? (double)rr_s.y + (double)rr_l.y : 0.0;
+    o[2] = lead ? (double)ra_s.x + (double)ra_l.x : 0.0;
+    o[3] = lead ? (double)ra_s.y + (double)ra_l.y : 0.0;
+    o[4] = lead ? nnd : 0.0;
   }
 };
 
@@ -769,14 +792,32 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   PV* VV = (PV*)(RB + (size_t)kStages * PEC);
   PC* SB = (PC*)(VV + (size_t)kStages * PEV);
 
-  const int n = st->n;
+  // pass coefficients in the working precision, converted once per CTA (FP64 is slow on this GPU)
+  struct Coefs {
+    typename O::Cplx a1, a2, aA;
+    typename O::Real zre, zim, mh1, mh2;
+    int n, hc;
+  };
+  __shared__ Coefs sc;
+  if (threadIdx.x == 0) {
+    sc.a1 = O::cplx(st->a1);
+    sc.a2 = O::cplx(st->a2);
+    sc.aA = O::cplx(st->aA);
+    const double2 Zs0 = st->Zs;
+    sc.zre = O::real(Zs0.x - p.hd);
+    sc.zim = O::real(Zs0.y);
+    sc.mh1 = O::real(-p.hk1);
+    sc.mh2 = O::real(-p.hk2);
+    sc.n = st->n;
+    sc.hc = st->hcnt;
+  }
+  __syncthreads();
+  const int n = sc.n;
   const int b1 = (n + 2) % 3, b2 = (n + 1) % 3, bo = n % 3;
   C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + bo) * d.nz * plane_elems;
-  const typename O::Cplx a1 = O::cplx(st->a1), a2 = O::cplx(st->a2), aA = O::cplx(st->aA);
-  const double2 Zs = st->Zs;
-  const typename O::Real zre = O::real(Zs.x - p.hd), zim = O::real(Zs.y);
-  const typename O::Real mh1 = O::real(-p.hk1), mh2 = O::real(-p.hk2);
-  const int hc = st->hcnt;
+  const typename O::Cplx a1 = sc.a1, a2 = sc.a2, aA = sc.aA;
+  const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
+  const int hc = sc.hc;
   H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + hc) * d.nb;
   const long long nxy = (long long)d.nx * d.ny;
 
