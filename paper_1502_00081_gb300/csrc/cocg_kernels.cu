@@ -8,7 +8,7 @@
 //
 // on a 2.5D tile that marches along z.  Each CTA owns a 32-wide x-y tile of one slot and a range
 // of z-planes.  A single thread streams every plane it needs with TMA (cp.async.bulk.tensor) into a
-// shared-memory ring guarded by mbarriers, kDepth planes ahead of the consumers: r_{n-1} on the tile
+// shared-memory ring guarded by mbarriers, up to 7 planes ahead of the consumers: r_{n-1} on the tile
 // plus a 2R halo, r_{n-2} and V_loc on the same box.  TMA's zero fill outside the tensor gives the
 // Dirichlet walls and the zero ghosts in z for free.  The threads keep each grid column's
 // z-neighbours in registers, evaluate A r_{n-1} and r_n on the tile plus R (the halo is recomputed
@@ -43,30 +43,33 @@
 #include "rsfd_internal.cuh"
 
 namespace rsfd {
-size_t pass_smem(int prec, int R, int tile_y);
+size_t pass_smem(int prec, int R, int tile_y, int depth);
 int pass_threads(int R, int tile_y);
 namespace {
 
 constexpr int kTileX = 32;       // interior tile width in x
 constexpr int kBoxX = 40;        // TMA box width in grid points (x0 - 4 ... x0 + 35)
 constexpr int kBoxOff = 4;       // the box starts kBoxOff points left of the tile
-constexpr int kDepth = 2;        // bundles (one plane of each input) in flight ahead of the consumers
-constexpr int kStages = kDepth + 1;
+constexpr int kMaxDepth = 7;     // bundles (one plane of each input) in flight ahead of the consumers
+constexpr int kMaxStages = kMaxDepth + 1;
 // threads per CTA of the pass kernel (fewer for double-float, which needs more registers per thread)
 template <int MODE> struct MaxThreads { static constexpr int value = 512; };
-template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 320; };
-template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 320; };
+template <> struct MaxThreads<RSFD_DF64> { static constexpr int value = 384; };
+template <> struct MaxThreads<RSFD_FP64> { static constexpr int value = 384; };
 constexpr long long kWaitCap = 1ll << 12;   // try_wait attempts before a wait is declared lost
 constexpr uint32_t kWaitHintNs = 1000000;    // suspend-time hint of one attempt (1 ms): cap ~ 4 s
 
 // ------------------------------------------------------------------------------------------------
 // packed FP32x2 helpers
 // ------------------------------------------------------------------------------------------------
-// Packed adds and subtracts are written as FFMA2 with a +-1 multiplier: one issued instruction and
-// the same single rounding as an add (the packed add instruction costs about two issue slots here).
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __ffma2_rn(a, make_float2(1.f, 1.f), b); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+// Packed adds and subtracts are written as FFMA2 with a +-1 multiplier held in constant memory:
+// one issued instruction with the single rounding of an add.  (A packed add, or an FFMA2 whose
+// multiplier the compiler can see is 1, costs two issue slots.)
+__constant__ float2 c_one2 = {1.f, 1.f};
+__constant__ float2 c_mone2 = {-1.f, -1.f};
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __ffma2_rn(a, c_one2, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, c_mone2, a); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return __fmul2_rn(a, c_mone2); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
@@ -449,7 +452,37 @@ struct AccDF {
   }
 };
 
+// complex64 vectors: rounded FP32 products with Kahan-compensated sums.  This mode is meant for the
+// regime where eps_32 * kappa is small (its SpMV error floor is eps_32 * kappa); there the rounded
+// products do not slow convergence, and they cost a fifth of the exact-product form.
+struct AccK {
+  float2 rr = make_float2(0.f, 0.f), rr_c = make_float2(0.f, 0.f);
+  float2 ra = make_float2(0.f, 0.f), ra_c = make_float2(0.f, 0.f);
+  float nn = 0.f;
+  static __device__ __forceinline__ void kahan(float2& s, float2& c, float2 term) {
+    const float2 y = f2sub(term, c);
+    const float2 t = f2add(s, y);
+    c = f2sub(f2sub(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void add(float2 r, float2 v) {
+    const float2 trr = make_float2(__fmaf_rn(r.x, r.x, -r.y * r.y), 2.f * r.x * r.y);
+    const float2 tra = make_float2(__fmaf_rn(r.x, v.x, -r.y * v.y), __fmaf_rn(r.x, v.y, r.y * v.x));
+    kahan(rr, rr_c, trr);
+    kahan(ra, ra_c, tra);
+    nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
+  }
+  __device__ __forceinline__ void get(double* o) {
+    o[0] = (double)rr.x - (double)rr_c.x;
+    o[1] = (double)rr.y - (double)rr_c.y;
+    o[2] = (double)ra.x - (double)ra_c.x;
+    o[3] = (double)ra.y - (double)ra_c.y;
+    o[4] = (double)nn;
+  }
+};
+
 template <int MODE> struct AccOf { typedef AccDF type; };
+template <> struct AccOf<RSFD_MIXED> { typedef AccK type; };
 template <> struct AccOf<RSFD_FP64> { typedef Acc<double> type; };
 
 // ------------------------------------------------------------------------------------------------
@@ -537,6 +570,7 @@ struct PassParams {
   double tol;
   int maxit;
   int hist_len;
+  int depth;                 // TMA bundles in flight ahead of the consumers (1 .. kMaxDepth)
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -746,11 +780,13 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   extern __shared__ unsigned char smem_raw[];
   __shared__ ScalarShared S;
   __shared__ int s_last, s_abort;
-  __shared__ __align__(8) unsigned long long bars[kStages];
+  __shared__ __align__(8) unsigned long long bars[kMaxStages];
 
   const int slot = blockIdx.y;
   SlotState* st = p.slots + slot;
   if (st->status != SLOT_RUNNING) return;
+  const int kDepth = p.depth;
+  const int kStages = kDepth + 1;
 
   // Each thread owns two x-adjacent grid points ("a pair").  Pairs of the middle region cover
   // x in [x0 - 2, x0 + 34) (18 pairs) and y in [y0 - R, y0 + TY + R); the tile proper is pairs
@@ -965,7 +1001,8 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   if (s_abort) {
     // drain the bundles still in flight before the CTA's shared memory is released
     if (tid == 0) {
-      for (int bnd = 0; bnd < issued; ++bnd) mbar_wait(smem_u32(&bars[bnd % kStages]), (uint32_t)((bnd / kStages) & 1));
+      for (int bnd = max(0, issued - kDepth); bnd < issued; ++bnd)
+        mbar_wait(smem_u32(&bars[bnd % kStages]), (uint32_t)((bnd / kStages) & 1));
     }
     return;
   }
@@ -1216,7 +1253,8 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.tol = tol;
   p.maxit = maxit;
   p.hist_len = hist_len;
-  const size_t smem = pass_smem(MODE, R, d.tile_y);
+  p.depth = d.depth;
+  const size_t smem = pass_smem(MODE, R, d.tile_y, d.depth);
   const int threads = pass_threads(R, d.tile_y);
   dim3 grid(d.ctas_per_slot, d.W), block(threads);
   pass_kernel<MODE, R><<<grid, block, smem, st>>>(p, *b.tmR, *b.tmV);
@@ -1229,12 +1267,14 @@ int pass_tile_x(int) { return kTileX; }
 int pass_box_x() { return kBoxX; }
 int pass_box_off() { return kBoxOff; }
 int pass_threads(int R, int tile_y) { return (18 * (tile_y + 2 * R) + 31) / 32 * 32; }
-size_t pass_smem(int prec, int R, int tile_y) {
+size_t pass_smem(int prec, int R, int tile_y, int depth) {
   const size_t es = prec == RSFD_MIXED ? 8 : 16, vs = prec == RSFD_MIXED ? 4 : 8;
   const size_t EY = (size_t)tile_y + 4 * R;
   const size_t pc = (kBoxX * EY * es + 127) & ~(size_t)127, pv = (kBoxX * EY * vs + 127) & ~(size_t)127;
-  return (size_t)(R + 1 + kDepth + kStages + R + 2) * pc + (size_t)kStages * pv + 128;
+  const size_t stages = (size_t)depth + 1;
+  return (size_t)(R + 1 + depth + stages + R + 2) * pc + stages * pv + 128;
 }
+int pass_max_depth() { return kMaxDepth; }
 int pass_max_threads(int prec) {
   if (prec == RSFD_DF64) return MaxThreads<RSFD_DF64>::value;
   if (prec == RSFD_FP64) return MaxThreads<RSFD_FP64>::value;

@@ -191,16 +191,28 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y) {
   return RSFD_OK;
 }
 
-static int default_tile_y(int prec, int R) {
-  if (prec == RSFD_MIXED) return 24;
-  return 12;
-}
-
 static bool tile_ok(int prec, int R, int tile_y) {
   if (tile_y < 1) return false;
   if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
   if (tile_y + 4 * R > 256) return false;
-  return pass_smem(prec, R, tile_y) <= (size_t)(216 * 1024);
+  return pass_smem(prec, R, tile_y, 2) <= (size_t)(216 * 1024);
+}
+
+// Tile height that minimises the rows computed per column of tiles, (tile_y + 2R) * ceil(Ny / tile_y),
+// among the heights the precision's CTA size and shared memory allow (ties to the taller tile).
+static int default_tile_y(int prec, int R, int ny) {
+  int best = 0;
+  long long best_rows = 0;
+  for (int ty = 4; ty <= 64; ty += 4) {
+    if (!tile_ok(prec, R, ty)) continue;
+    const long long rows = (long long)(ty + 2 * R) * ((ny + ty - 1) / ty);
+    if (best == 0 || rows <= best_rows) {
+      best = ty;
+      best_rows = rows;
+    }
+    if (ty >= ny) break;
+  }
+  return best > 0 ? best : 4;
 }
 
 }  // namespace rsfd
@@ -368,18 +380,36 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.nb = h->nb;
   d.K = K;
   d.ncols = ncols;
-  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R);
+  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny);
   if (!tile_ok(prec, h->R, d.tile_y)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
-  d.zchunk = h->opts.z_chunk > 0 ? h->opts.z_chunk : std::min(h->nz, 32);
+  // deepest TMA prefetch that fits in shared memory: more planes in flight hide the load latency of a
+  // CTA that is alone on its SM
+  d.depth = 2;
+  for (int dp = pass_max_depth(); dp >= 2; --dp)
+    if (pass_smem(prec, h->R, d.tile_y, dp) <= (size_t)(216 * 1024)) {
+      d.depth = dp;
+      break;
+    }
   d.tiles_x = (h->nx + pass_tile_x(h->R) - 1) / pass_tile_x(h->R);
   d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
+  int W0 = h->opts.slots > 0 ? h->opts.slots : 256;
+  W0 = std::min(W0, ncols);
+  if (h->opts.z_chunk > 0) {
+    d.zchunk = h->opts.z_chunk;
+  } else {
+    // whole z-columns per CTA (no pipeline refill) unless that leaves fewer than ~4 CTAs per SM
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    d.zchunk = h->nz;
+    while (d.zchunk > 16 && (long long)d.tiles_x * d.tiles_y * ((h->nz + d.zchunk - 1) / d.zchunk) * W0 < 4LL * sms)
+      d.zchunk = (d.zchunk + 1) / 2;
+  }
   d.nzchunks = (h->nz + d.zchunk - 1) / d.zchunk;
   d.ctas_per_slot = d.tiles_x * d.tiles_y * d.nzchunks;
   const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
   if (C > kMaxHist) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: iters_per_sync too large");
   const long long vec = (long long)h->nxp * h->ny * h->nz;
-  int W = h->opts.slots > 0 ? h->opts.slots : 64;
-  W = std::min(W, ncols);
+  int W = W0;
   {
     size_t freeb = 0, totb = 0;
     RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));

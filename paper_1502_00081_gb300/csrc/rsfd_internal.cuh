@@ -102,6 +102,7 @@ struct SolveDims {
   int K;              // energies
   int W;              // slots
   int tile_y;         // stencil tile height (y); the tile width in x is fixed by the kernel
+  int depth;          // TMA prefetch depth of the pass kernel
   int tiles_x, tiles_y, zchunk, nzchunks, ctas_per_slot;
   int ncols;
 };
@@ -153,7 +154,8 @@ cudaError_t launch_writeout(int prec, const SolveDims& d, const SolverBuffers& b
 size_t vec_elem_bytes(int prec);
 size_t pot_elem_bytes(int prec);
 size_t hist_elem_bytes(int prec);
-size_t pass_smem(int prec, int R, int tile_y);
+size_t pass_smem(int prec, int R, int tile_y, int depth);
+int pass_max_depth();
 int pass_box_x();
 int pass_box_off();
 int pass_max_threads(int prec);
