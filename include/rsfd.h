@@ -100,17 +100,28 @@ typedef struct {
   int32_t final_seed; /* energy index of the seed when the column finished */
 } rsfd_col_info;
 
+/* Form of the seed iteration's pass (rsfd_solve_opts.pass_kind). */
+typedef enum {
+  RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED for RSFD_FP64 and RSFD_DF64, RSFD_PASS_RECOMPUTE for RSFD_MIXED */
+  RSFD_PASS_RECOMPUTE = 1, /* three vectors per iteration (r_{n-1}, r_{n-2} in, r_n out); A r_{n-1} is
+                              recomputed on the tile plus halo and A r_n again for the dot products */
+  RSFD_PASS_STORED = 2     /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);
+                              one stencil application per grid point */
+} rsfd_pass_kind;
+
 /* Launch options of the solver; zero fields mean "choose automatically". */
 typedef struct {
   int32_t slots;          /* columns iterated together (RHS block width) */
   int32_t iters_per_sync; /* iterations per CUDA-graph replay between host checks; also the number of
                              iterations collapsed into one shift update (<= 64) */
-  int32_t tile_y;         /* stencil tile height in y; RSFD_ERR_ARG when the CTA would exceed 768 threads
-                             (512 for RSFD_DF64) or 220 KB of shared memory */
+  int32_t tile_y;         /* stencil tile height in y; RSFD_ERR_ARG when the pass's CTA would exceed its
+                             thread limit or 216 KB of shared memory */
   int32_t z_chunk;        /* planes per CTA along z */
   int32_t use_graphs;     /* 1 = capture iteration chunks in CUDA graphs (default), -1 = plain launches */
   int32_t profile;        /* 1 = time every kernel launch with CUDA events on the launching stream
                              (event nodes inside the CUDA graph); results in rsfd_get_stats */
+  int32_t pass_kind;      /* rsfd_pass_kind */
+  int32_t prefetch;       /* z-planes of input the pass keeps in flight (TMA), 1..7 */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

@@ -27,6 +27,9 @@ RSFD_DF64 = 2
 RSFD_SEED_MID = 0
 RSFD_SEED_FIRST = 1
 RSFD_SEED_INDEX = 2
+RSFD_PASS_AUTO = 0
+RSFD_PASS_RECOMPUTE = 1
+RSFD_PASS_STORED = 2
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED", 5: "ERR_BREAKDOWN",
            6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
@@ -51,7 +54,8 @@ class rsfd_col_info(ctypes.Structure):
 
 class rsfd_solve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32)]
 
 
 class rsfd_stats(ctypes.Structure):
@@ -180,9 +184,11 @@ def rsfd_boundary_rows(h):
     return rows
 
 
-def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0):
+def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0,
+                           pass_kind=0, prefetch=0):
     lib = load_library()
-    o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile))
+    o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile),
+                        int(pass_kind), int(prefetch))
     _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
 
 

@@ -267,6 +267,18 @@ __device__ __forceinline__ void dfacc_mul(DFAcc& a, dfr c, const dfc& x) {
   a.s = t;
   a.lo = f2add(a.lo, f2sub(te, ne));
 }
+// a fresh accumulator holding c x (the exact leading product and its low-order terms)
+__device__ __forceinline__ DFAcc dfacc_prod(dfr c, const dfc& x) {
+  const float2 nch = bc(-c.h);
+  const float2 p = f2mul(bc(c.h), x.h);
+  float2 ne = f2fma(nch, x.h, p);
+  ne = f2fma(nch, x.l, ne);
+  ne = f2fma(bc(-c.l), x.h, ne);
+  DFAcc a;
+  a.s = p;
+  a.lo = f2neg(ne);
+  return a;
+}
 __device__ __forceinline__ dfc dfacc_get(const DFAcc& a) {
   dfc r;
   fast_two_sum2(a.s, a.lo, r.h, r.l);
@@ -320,8 +332,7 @@ template <int R> struct Stencil<RSFD_DF64, R> {
   }
   static __device__ __forceinline__ dfc applyA(const dfc& c, const dfc (&n1)[6], const dfc (&n2)[6], float2 v,
                                                dfr zre, dfr zim, dfr mh1, dfr mh2) {
-    DFAcc a = dfacc_zero();
-    dfacc_mul(a, mh1, sum6(n1));
+    DFAcc a = dfacc_prod(mh1, sum6(n1));
     if (R == 2) dfacc_mul(a, mh2, sum6(n2));
     dfacc_mul(a, dfr_sub(zre, v.x, v.y), c);
     dfacc_mul(a, zim, df_swapneg(c));
@@ -329,8 +340,7 @@ template <int R> struct Stencil<RSFD_DF64, R> {
   }
   static __device__ __forceinline__ dfc combine(const dfz& a1, const dfc& r1, const dfz& a2, const dfc& r2,
                                                 const dfz& aA, const dfc& u) {
-    DFAcc a = dfacc_zero();
-    dfacc_mul(a, a1.re, r1);
+    DFAcc a = dfacc_prod(a1.re, r1);
     dfacc_mul(a, a1.im, df_swapneg(r1));
     dfacc_mul(a, a2.re, r2);
     dfacc_mul(a, a2.im, df_swapneg(r2));
@@ -388,7 +398,16 @@ template <> struct Acc<double> {
     ra_y = fma(r.x, v.y, fma(r.y, v.x, ra_y));
     nn = fma(r.x, r.x, fma(r.y, r.y, nn));
   }
-  __device__ __forceinline__ void get(double* o) const { o[0] = rr_x; o[1] = rr_y; o[2] = ra_x; o[3] = ra_y; o[4] = nn; }
+  // warp sums (whole warps only); lane 0 returns them, the other lanes zeros
+  __device__ __forceinline__ void get(double* o) const {
+    double t[5] = {rr_x, rr_y, ra_x, ra_y, nn};
+    const bool lead = (threadIdx.x & 31) == 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      for (int off = 16; off > 0; off >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], off);
+      o[k] = lead ? t[k] : 0.0;
+    }
+  }
 };
 
 // FP32-based accumulators (complex64 and double-float vectors).  The unconjugated forms cancel
@@ -441,8 +460,8 @@ struct AccDF {
       merge(rr_s, rr_l, a, b);
       merge(ra_s, ra_l, c, d);
     }
-    double nnd = (double)nn;
-    for (int off = 16; off > 0; off >>= 1) nnd += __shfl_down_sync(0xffffffffu, nnd, off);
+    for (int off = 16; off > 0; off >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, off);
+    const double nnd = (double)nn;
     const bool lead = (threadIdx.x & 31) == 0;
     o[0] = lead ? (double)rr_s.x + (double)rr_l.x : 0.0;
     o[1] = lead ? (double)rr_s.y + (double)rr_l.y : 0.0;
@@ -472,12 +491,23 @@ struct AccK {
     kahan(ra, ra_c, tra);
     nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
   }
+  // The Kahan pairs (s, -c) are double-float values: reduce them over the warp with TwoSum merges
+  // (whole warps only) and convert once; lane 0 returns the warp's sums, the other lanes zeros.
   __device__ __forceinline__ void get(double* o) {
-    o[0] = (double)rr.x - (double)rr_c.x;
-    o[1] = (double)rr.y - (double)rr_c.y;
-    o[2] = (double)ra.x - (double)ra_c.x;
-    o[3] = (double)ra.y - (double)ra_c.y;
-    o[4] = (double)nn;
+    float2 rl = f2neg(rr_c), al = f2neg(ra_c);
+    for (int off = 16; off > 0; off >>= 1) {
+      const float2 a = AccDF::shfl2(rr, off), b = AccDF::shfl2(rl, off), c = AccDF::shfl2(ra, off),
+                   e = AccDF::shfl2(al, off);
+      AccDF::merge(rr, rl, a, b);
+      AccDF::merge(ra, al, c, e);
+      nn += __shfl_down_sync(0xffffffffu, nn, off);
+    }
+    const bool lead = (threadIdx.x & 31) == 0;
+    o[0] = lead ? (double)rr.x + (double)rl.x : 0.0;
+    o[1] = lead ? (double)rr.y + (double)rl.y : 0.0;
+    o[2] = lead ? (double)ra.x + (double)al.x : 0.0;
+    o[3] = lead ? (double)ra.y + (double)al.y : 0.0;
+    o[4] = lead ? (double)nn : 0.0;
   }
 };
 
@@ -534,21 +564,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-// Sum NV doubles over the (whole-warp) block; result valid in thread 0.  s_red holds 32*NV doubles.
+// Sum over the block of per-warp values held by lane 0 of each warp (the accumulators' get() leaves
+// the warp sums there); fixed order over the warps.  The sums are valid in thread 0.
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* s_red) {
+__device__ __forceinline__ void block_sum_lane0(double (&v)[NV], double* s_red) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) s_red[wid * NV + k] = v[k];
   }
   __syncthreads();
-  if (wid == 0) {
+  if (tid == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum((lane < nw) ? s_red[lane * NV + k] : 0.0);
+    for (int k = 0; k < NV; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += s_red[w * NV + k];
+      v[k] = t;
+    }
   }
   __syncthreads();
 }
@@ -571,6 +604,8 @@ struct PassParams {
   int maxit;
   int hist_len;
   int depth;                 // TMA bundles in flight ahead of the consumers (1 .. kMaxDepth)
+  int stored_u;              // 1: the pass reads the stored A r_{n-1} (seed switches fold the energy
+                             //    shift of the stored product into a1)
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -749,7 +784,12 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
   }
   if (tid == 0) {
     const double2 c = S.c;
-    st->a1 = cmul(cadd(one, c), S.scale_n);
+    double2 a1 = cmul(cadd(one, c), S.scale_n);
+    if (p.stored_u && S.do_switch) {
+      // the stored product is A r_n with the previous seed's energy: A~ r_n = A r_n + (Z_s~ - Z_s) r_n
+      a1 = csub(a1, cmul(cmul(S.alpha, S.scale_n), csub(S.Zs, st->Zs)));
+    }
+    st->a1 = a1;
     st->a2 = cmul(make_double2(-c.x, -c.y), S.scale_nm1);
     st->aA = cmul(make_double2(-S.alpha.x, -S.alpha.y), S.scale_n);
     st->Zs = S.Zs;
@@ -762,6 +802,43 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
     st->n = S.n + 1;
     atomicAdd(&p.counters[1], 1ull);
   }
+}
+
+// Per-CTA partial sums (lane 0 of each warp holds its warp's sums) -> the slot's partial array ->
+// atomic ticket; the last CTA of the slot sums the partials in CTA order (warp 0, fixed tree) and
+// returns true with (r,r), (r,Ar), ||r||^2 in S.  No CTA waits on another.
+__device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)[5], ScalarShared& S, int& s_last) {
+  const int tid = threadIdx.x;
+  block_sum_lane0<5>(v5, S.red);
+  if (tid == 0) {
+    double* dst = p.partials + ((size_t)slot * p.d.ctas_per_slot + cta) * 8;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dst[k] = v5[k];
+    __threadfence();
+    const unsigned int t = atomicAdd(p.tickets + slot, 1u);
+    s_last = (t == (unsigned int)(p.d.ctas_per_slot - 1));
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  if (tid < 32) {
+    double w5[5] = {0, 0, 0, 0, 0};
+    const double* src = p.partials + (size_t)slot * p.d.ctas_per_slot * 8;
+    for (int k = tid; k < p.d.ctas_per_slot; k += 32) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) w5[j] += __ldcg(src + (size_t)k * 8 + j);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w5[j] = warp_sum(w5[j]);
+    if (tid == 0) {
+      S.rr = make_double2(w5[0], w5[1]);
+      S.rAr = make_double2(w5[2], w5[3]);
+      S.nrm2 = w5[4];
+      p.tickets[slot] = 0u;
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -850,7 +927,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   __syncthreads();
   const int n = sc.n;
   const int b1 = (n + 2) % 3, b2 = (n + 1) % 3, bo = n % 3;
-  C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + bo) * d.nz * plane_elems;
+  C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + bo) * d.nz * plane_elems;   // nvec = 3
   const typename O::Cplx a1 = sc.a1, a2 = sc.a2, aA = sc.aA;
   const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
   const int hc = sc.hc;
@@ -881,7 +958,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     s_abort = 0;
   }
   __syncthreads();
-  int issued = 0;
+  int issued = 0, s_fail = 0;
   if (tid == 0) {
     for (int bnd = 0; bnd < kDepth && bnd < nsteps; ++bnd) issue(bnd);
     issued = min(kDepth, nsteps);
@@ -913,6 +990,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       s_abort = 1;
       atomicExch(p.error_flag, 1);
     }
+    s_fail = s;
     const int c = z0 - 3 * R + s;          // centre plane of A r_{n-1} and r_n in this step
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) { qa[k] = qa[k + 1]; vq[k] = vq[k + 1]; }
@@ -999,9 +1077,10 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     isv = (isv + 1 == NSB) ? 0 : isv + 1;
   }
   if (s_abort) {
-    // drain the bundles still in flight before the CTA's shared memory is released
+    // drain the bundles still in flight (the one whose wait expired and those issued after it)
+    // before the CTA's shared memory is released
     if (tid == 0) {
-      for (int bnd = max(0, issued - kDepth); bnd < issued; ++bnd)
+      for (int bnd = s_fail; bnd < issued; ++bnd)
         mbar_wait(smem_u32(&bars[bnd % kStages]), (uint32_t)((bnd / kStages) & 1));
     }
     return;
@@ -1009,35 +1088,231 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
 
   double v5[5];
   acc.get(v5);
-  block_sum<5>(v5, S.red);
-  if (tid == 0) {
-    double* dst = p.partials + ((size_t)slot * d.ctas_per_slot + cta) * 8;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) dst[k] = v5[k];
-    __threadfence();
-    const unsigned int t = atomicAdd(p.tickets + slot, 1u);
-    s_last = (t == (unsigned int)(d.ctas_per_slot - 1));
+  if (pass_finish(p, slot, cta, v5, S, s_last)) scalar_step(p, slot, S);
+}
+
+// ------------------------------------------------------------------------------------------------
+// the stored-product pass
+// ------------------------------------------------------------------------------------------------
+// One seed iteration that keeps u = A r in HBM next to r:
+//
+//   r_n = a1 r_{n-1} + a2 r_{n-2} + aA u_{n-1}     (pointwise, Eq. rvec with u_{n-1} = A r_{n-1})
+//   u_n = A r_n                                     (one stencil application per grid point)
+//
+// It moves five vectors per iteration (reads r_{n-1}, r_{n-2}, u_{n-1}; writes r_n, u_n) against
+// three for the fused pass, but applies the stencil once per point instead of on the tile plus
+// halo and again for the dots; in double-float arithmetic the stencil dominates, so this is the
+// faster form there.  Tile: 32 x TY points in x-y, one warp per tile row, plus halo warps that
+// evaluate r_n on the R-wide frame the stencil needs (the x-y box is 36 x (TY + 2R) points, TMA
+// loaded from x0 - 2).  Along z the r_n values of a thread's own column stay in registers.
+constexpr int kUBoxX = 36;
+constexpr int kUBoxOff = 2;
+template <int MODE> struct MaxThreadsU { static constexpr int value = 704; };
+
+template <int MODE, int R>
+__global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassParams p,
+                                                                        const __grid_constant__ CUtensorMap tmR,
+                                                                        const __grid_constant__ CUtensorMap tmV) {
+  typedef Ops<MODE> O;
+  typedef Stencil<MODE, R> ST;
+  typedef typename O::C C;
+  typedef typename O::VT VT;
+  typedef typename O::H H;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ ScalarShared S;
+  __shared__ int s_last, s_abort;
+  __shared__ __align__(8) unsigned long long bars[kMaxStages];
+
+  const int slot = blockIdx.y;
+  SlotState* st = p.slots + slot;
+  if (st->status != SLOT_RUNNING) return;
+  const int kDepth = p.depth;
+  const int kStages = kDepth + 1;
+  const SolveDims& d = p.d;
+  const int TY = d.tile_y;
+  const int EY = TY + 2 * R;
+  constexpr int BW = kUBoxX;
+  const int tid = threadIdx.x;
+  const int cta = blockIdx.x;
+  const int tz = cta % d.nzchunks;
+  const int txy = cta / d.nzchunks;
+  const int tx = txy % d.tiles_x, ty = txy / d.tiles_x;
+  const int z0 = tz * d.zchunk;
+  const int z1 = min(z0 + d.zchunk, d.nz);
+  const int x0 = tx * kTileX, y0 = ty * TY;
+  const int nint = kTileX * TY;
+
+  // this thread's point in the box: a tile point (warp = tile row) or a frame point
+  const bool interior = tid < nint;
+  int cx = -1, cy = 0;
+  if (interior) {
+    cx = (tid & 31) + kUBoxOff;
+    cy = (tid >> 5) + R;
+  } else {
+    const int hh = tid - nint;
+    if (hh < 2 * R * TY) {                       // R columns left and right of every tile row
+      const int side = hh / (R * TY), k = hh - side * R * TY;
+      cy = k / R + R;
+      cx = side == 0 ? kUBoxOff - R + k % R : kUBoxOff + kTileX + k % R;
+    } else if (hh < 2 * R * TY + 2 * R * kTileX) {   // R rows below and above the tile
+      const int k2 = hh - 2 * R * TY;
+      const int side = k2 / (R * kTileX), k = k2 - side * R * kTileX;
+      cx = kUBoxOff + k % kTileX;
+      cy = side == 0 ? k / kTileX : TY + R + k / kTileX;
+    }
+  }
+  const bool has_pt = cx >= 0;
+  const int sidx = cy * BW + cx;
+  const int gx = x0 + (tid & 31), gy = y0 + (tid >> 5);
+  const bool own = interior && gx < d.nx && gy < d.ny;
+  const long long plane_elems = (long long)d.nxp * d.ny;
+
+  // shared memory: per stage the boxes of r_{n-1}, r_{n-2}, u_{n-1} (plane q) and the tile of V
+  // (plane q - R); a ring of R + 2 planes of r_n
+  const size_t PBb = (size_t)BW * EY * sizeof(C);
+  const size_t PVb = (size_t)kTileX * TY * sizeof(VT);
+  const int PE = (int)(((PBb + 127) & ~(size_t)127) / sizeof(C));
+  const int PEV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(VT));
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  C* RA = (C*)base;
+  C* RB = RA + (size_t)kStages * PE;
+  C* UA = RB + (size_t)kStages * PE;
+  C* SB = UA + (size_t)kStages * PE;
+  VT* VV = (VT*)(SB + (size_t)(R + 2) * PE);
+
+  struct Coefs {
+    typename O::Cplx a1, a2, aA;
+    typename O::Real zre, zim, mh1, mh2;
+    int n, hc;
+  };
+  __shared__ Coefs sc;
+  if (threadIdx.x == 0) {
+    sc.a1 = O::cplx(st->a1);
+    sc.a2 = O::cplx(st->a2);
+    sc.aA = O::cplx(st->aA);
+    const double2 Zs0 = st->Zs;
+    sc.zre = O::real(Zs0.x - p.hd);
+    sc.zim = O::real(Zs0.y);
+    sc.mh1 = O::real(-p.hk1);
+    sc.mh2 = O::real(-p.hk2);
+    sc.n = st->n;
+    sc.hc = st->hcnt;
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  {
-    double w5[5] = {0, 0, 0, 0, 0};
-    const double* src = p.partials + (size_t)slot * d.ctas_per_slot * 8;
-    for (int k = tid; k < d.ctas_per_slot; k += blockDim.x) {
+  const int n = sc.n;
+  const int i1 = (n + 2) % 3, i2 = (n + 1) % 3, io = n % 3;
+  const int iu1 = 3 + (n + 1) % 2, iuo = 3 + n % 2;
+  const long long vec = (long long)d.nz * plane_elems;
+  C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + io) * vec;
+  C* uout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + iuo) * vec;
+  const typename O::Cplx a1 = sc.a1, a2 = sc.a2, aA = sc.aA;
+  const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
+  H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + sc.hc) * d.nb;
+  const long long nxy = (long long)d.nx * d.ny;
+
+  constexpr int mR = (MODE == RSFD_DF64) ? 4 : 2;
+  constexpr int mV = (MODE == RSFD_DF64) ? 2 : 1;
+  const int xr = mR * (x0 - kUBoxOff), xv = mV * x0, yb = y0 - R;
+  const uint32_t bundle_bytes = (uint32_t)(3 * PBb + PVb);
+  const int nsteps = (z1 - z0) + 2 * R;
+  const int w1 = slot * 5 + i1, w2 = slot * 5 + i2, wu = slot * 5 + iu1;
+
+  auto issue = [&](int bnd) {
+    const int q = z0 - R + bnd;
+    const int k = bnd % kStages;
+    const uint32_t bar = smem_u32(&bars[k]);
+    mbar_expect_tx(bar, bundle_bytes);
+    tma_load_4d(smem_u32(RA + (size_t)k * PE), &tmR, xr, yb, q, w1, bar);
+    tma_load_4d(smem_u32(RB + (size_t)k * PE), &tmR, xr, yb, q, w2, bar);
+    tma_load_4d(smem_u32(UA + (size_t)k * PE), &tmR, xr, yb, q, wu, bar);
+    tma_load_3d(smem_u32(VV + (size_t)k * PEV), &tmV, xv, y0, q - R, bar);
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  int issued = 0, s_fail = 0;
+  if (tid == 0) {
+    for (int bnd = 0; bnd < kDepth && bnd < nsteps; ++bnd) issue(bnd);
+    issued = min(kDepth, nsteps);
+  }
+
+  C zq[2 * R + 1];   // r_n on planes c - R .. c + R of this thread's column
 #pragma unroll
-      for (int j = 0; j < 5; ++j) w5[j] += __ldcg(src + (size_t)k * 8 + j);
+  for (int k = 0; k <= 2 * R; ++k) zq[k] = O::zero();
+  typename AccOf<MODE>::type acc;
+  // ring positions: ist = s % kStages, par = (s / kStages) & 1, isw = s % (R + 2), isr = (s - R) % (R + 2)
+  int ist = 0, par = 0, isw = 0, isr = 2 % (R + 2);
+
+  for (int s = 0; s < nsteps; ++s) {
+    if (tid == 0 && s + kDepth < nsteps) {
+      issue(s + kDepth);
+      issued = s + kDepth + 1;
     }
-    block_sum<5>(w5, S.red);
-    if (tid == 0) {
-      S.rr = make_double2(w5[0], w5[1]);
-      S.rAr = make_double2(w5[2], w5[3]);
-      S.nrm2 = w5[4];
-      p.tickets[slot] = 0u;
+    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
+      s_abort = 1;
+      atomicExch(p.error_flag, 1);
+    }
+    s_fail = s;
+    // r_n on plane q = z0 - R + s at this thread's point (zero outside the grid: TMA zero fill)
+    C rq = O::zero();
+    VT vc = VT();
+    if (has_pt) {
+      const size_t o = (size_t)ist * PE + sidx;
+      rq = ST::combine(a1, RA[o], a2, RB[o], aA, UA[o]);                     // Eq. rvec
+      SB[(size_t)isw * PE + sidx] = rq;
+    }
+    if (interior) {
+#pragma unroll
+      for (int k = 0; k < 2 * R; ++k) zq[k] = zq[k + 1];
+      zq[2 * R] = rq;
+      vc = VV[(size_t)ist * PEV + tid];
     }
     __syncthreads();
+    if (s_abort) break;
+    const int c = z0 - 2 * R + s;      // plane of this step's u_n = A r_n
+    if (own && s >= 2 * R) {
+      const C* P = SB + (size_t)isr * PE;
+      const C n1[6] = {zq[R - 1], zq[R + 1], P[sidx - 1], P[sidx + 1], P[sidx - BW], P[sidx + BW]};
+      C n2[6];
+      if (R == 2) {
+        n2[0] = zq[0]; n2[1] = zq[2 * R]; n2[2] = P[sidx - 2]; n2[3] = P[sidx + 2];
+        n2[4] = P[sidx - 2 * BW]; n2[5] = P[sidx + 2 * BW];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) n2[k] = O::zero();
+      }
+      const C rc = zq[R];
+      const C u = ST::applyA(rc, n1, n2, vc, zre, zim, mh1, mh2);
+      acc.add(rc, u);
+      const size_t g = (size_t)c * plane_elems + (size_t)gy * d.nxp + gx;
+      rout[g] = rc;
+      uout[g] = u;
+      int pl = -1;
+      if (c < d.nface) pl = c;
+      else if (c >= d.nz - d.nface) pl = c - d.nz + 2 * d.nface;
+      if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gy * d.nx + gx] = O::hi(rc);
+    }
+    if (++ist == kStages) { ist = 0; par ^= 1; }
+    isw = (isw + 1 == R + 2) ? 0 : isw + 1;
+    isr = (isr + 1 == R + 2) ? 0 : isr + 1;
   }
-  scalar_step(p, slot, S);
+  if (s_abort) {
+    // drain the bundles still in flight (the one whose wait expired and those issued after it)
+    // before the CTA's shared memory is released
+    if (tid == 0) {
+      for (int bnd = s_fail; bnd < issued; ++bnd)
+        mbar_wait(smem_u32(&bars[bnd % kStages]), (uint32_t)((bnd / kStages) & 1));
+    }
+    return;
+  }
+  double v5[5];
+  acc.get(v5);
+  if (pass_finish(p, slot, cta, v5, S, s_last)) scalar_step(p, slot, S);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1162,11 +1437,19 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
   const long long jp = (jz * d.ny + jy) * d.nxp + jx;
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
-  C* r1 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 1) * vec;   // r_{-2}
-  C* r2 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 3 + 2) * vec;   // r_{-1}
+  C* r1 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * d.nvec + 1) * vec;   // r_{-2}
+  C* r2 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * d.nvec + 2) * vec;   // r_{-1}
   for (long long t = gt; t < vec; t += gs) {
     r1[t] = Ops<MODE>::zero();
     r2[t] = (t == jp) ? Ops<MODE>::unit() : Ops<MODE>::zero();
+  }
+  if (d.nvec == 5) {   // stored products A r: the first pass multiplies u_{-1} by aA = 0
+    C* u0 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + 3) * vec;
+    C* u1 = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + 4) * vec;
+    for (long long t = gt; t < vec; t += gs) {
+      u0[t] = Ops<MODE>::zero();
+      u1[t] = Ops<MODE>::zero();
+    }
   }
   X* xx = reinterpret_cast<X*>(p.xbuf) + (size_t)slot * d.K * d.nb;
   X* pp = reinterpret_cast<X*>(p.pbuf) + (size_t)slot * d.K * d.nb;
@@ -1254,10 +1537,15 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.maxit = maxit;
   p.hist_len = hist_len;
   p.depth = d.depth;
-  const size_t smem = pass_smem(MODE, R, d.tile_y, d.depth);
-  const int threads = pass_threads(R, d.tile_y);
-  dim3 grid(d.ctas_per_slot, d.W), block(threads);
-  pass_kernel<MODE, R><<<grid, block, smem, st>>>(p, *b.tmR, *b.tmV);
+  p.stored_u = d.kind == RSFD_PASS_STORED;
+  dim3 grid(d.ctas_per_slot, d.W);
+  if (d.kind == RSFD_PASS_STORED) {
+    const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth);
+    passu_kernel<MODE, R><<<grid, passu_threads(R, d.tile_y), smem, st>>>(p, *b.tmR, *b.tmV);
+  } else {
+    const size_t smem = pass_smem(MODE, R, d.tile_y, d.depth);
+    pass_kernel<MODE, R><<<grid, pass_threads(R, d.tile_y), smem, st>>>(p, *b.tmR, *b.tmV);
+  }
   return cudaGetLastError();
 }
 
@@ -1275,6 +1563,22 @@ size_t pass_smem(int prec, int R, int tile_y, int depth) {
   return (size_t)(R + 1 + depth + stages + R + 2) * pc + stages * pv + 128;
 }
 int pass_max_depth() { return kMaxDepth; }
+int passu_box_x() { return kUBoxX; }
+int passu_box_off() { return kUBoxOff; }
+// tile rows (one warp each) plus the warps of the R-wide frame: 2 R TY + 2 R 32 points
+int passu_threads(int R, int tile_y) { return 32 * tile_y + (2 * R * tile_y + 2 * R * kTileX + 31) / 32 * 32; }
+size_t passu_smem(int prec, int R, int tile_y, int depth) {
+  const size_t es = prec == RSFD_MIXED ? 8 : 16, vs = prec == RSFD_MIXED ? 4 : 8;
+  const size_t pb = ((size_t)kUBoxX * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
+  const size_t pv = ((size_t)kTileX * tile_y * vs + 127) & ~(size_t)127;
+  const size_t stages = (size_t)depth + 1;
+  return stages * (3 * pb + pv) + (size_t)(R + 2) * pb + 128;
+}
+int passu_max_threads(int prec) {
+  if (prec == RSFD_DF64) return MaxThreadsU<RSFD_DF64>::value;
+  if (prec == RSFD_FP64) return MaxThreadsU<RSFD_FP64>::value;
+  return MaxThreadsU<RSFD_MIXED>::value;
+}
 int pass_max_threads(int prec) {
   if (prec == RSFD_DF64) return MaxThreads<RSFD_DF64>::value;
   if (prec == RSFD_FP64) return MaxThreads<RSFD_FP64>::value;
@@ -1285,7 +1589,8 @@ cudaError_t kernels_init() {
   const int lim = 216 * 1024;
   cudaError_t e = cudaSuccess;
 #define RSFD_ATTR(M, R)                                                                                  \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(passu_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   RSFD_ATTR(RSFD_FP64, 1)
   RSFD_ATTR(RSFD_FP64, 2)
   RSFD_ATTR(RSFD_MIXED, 1)

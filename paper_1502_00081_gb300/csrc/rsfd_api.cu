@@ -158,20 +158,26 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// TMA descriptors of the Krylov vectors [3W][Nz][Ny][Nxp] and of the potential [Nz][Ny][Nxp].
+// TMA descriptors of the Krylov vectors [nvec W][Nz][Ny][Nxp] and of the potential [Nz][Ny][Nxp].
 // Rows are padded to Nxp (a multiple of 4) so every stride is a multiple of 16 bytes; the x extent
 // is the true Nx, so reads past the last column (and outside the grid) come back as zeros.
-static rsfd_status make_maps(Handle* h, int W, int tile_y) {
+// Boxes: fused pass 40 x (tile_y + 4R) for both; stored-product pass 36 x (tile_y + 2R) for the
+// vectors and the 32 x tile_y tile for the potential.
+static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const bool f64 = h->prec == RSFD_FP64;
   const CUtensorMapDataType dt = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint64_t es = f64 ? 8 : 4;
   const cuuint64_t mR = h->prec == RSFD_DF64 ? 4 : 2, mV = h->prec == RSFD_DF64 ? 2 : 1;
-  const cuuint32_t EY = (cuuint32_t)(tile_y + 4 * h->R);
-  const cuuint32_t BX = (cuuint32_t)pass_box_x();
+  const bool stored = kind == RSFD_PASS_STORED;
+  const cuuint64_t nvec = stored ? 5 : 3;
+  const cuuint32_t EY = (cuuint32_t)(tile_y + (stored ? 2 : 4) * h->R);
+  const cuuint32_t BX = (cuuint32_t)(stored ? passu_box_x() : pass_box_x());
+  const cuuint32_t VBX = (cuuint32_t)(stored ? pass_tile_x(h->R) : pass_box_x());
+  const cuuint32_t VBY = stored ? (cuuint32_t)tile_y : EY;
   {
-    cuuint64_t dims[4] = {mR * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz, (cuuint64_t)3 * W};
+    cuuint64_t dims[4] = {mR * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz, nvec * W};
     cuuint64_t strides[3] = {mR * h->nxp * es, mR * h->nxp * es * h->ny, mR * h->nxp * es * h->ny * h->nz};
     cuuint32_t box[4] = {(cuuint32_t)(mR * BX), EY, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -182,7 +188,7 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y) {
   {
     cuuint64_t dims[3] = {mV * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz};
     cuuint64_t strides[2] = {mV * h->nxp * es, mV * h->nxp * es * h->ny};
-    cuuint32_t box[3] = {(cuuint32_t)(mV * BX), EY, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(mV * VBX), VBY, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(&h->tmV, dt, 3, h->dV, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -191,20 +197,33 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y) {
   return RSFD_OK;
 }
 
-static bool tile_ok(int prec, int R, int tile_y) {
+static int resolve_kind(int prec, int opt) {
+  if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED) return opt;
+  return prec == RSFD_MIXED ? RSFD_PASS_RECOMPUTE : RSFD_PASS_STORED;
+}
+
+static size_t kind_smem(int prec, int R, int tile_y, int depth, int kind) {
+  return kind == RSFD_PASS_STORED ? passu_smem(prec, R, tile_y, depth) : pass_smem(prec, R, tile_y, depth);
+}
+
+static bool tile_ok(int prec, int R, int tile_y, int kind) {
   if (tile_y < 1) return false;
-  if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
+  if (kind == RSFD_PASS_STORED) {
+    if (passu_threads(R, tile_y) > passu_max_threads(prec)) return false;
+  } else {
+    if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
+  }
   if (tile_y + 4 * R > 256) return false;
-  return pass_smem(prec, R, tile_y, 2) <= (size_t)(216 * 1024);
+  return kind_smem(prec, R, tile_y, 1, kind) <= (size_t)(216 * 1024);
 }
 
 // Tile height that minimises the rows computed per column of tiles, (tile_y + 2R) * ceil(Ny / tile_y),
-// among the heights the precision's CTA size and shared memory allow (ties to the taller tile).
-static int default_tile_y(int prec, int R, int ny) {
+// among the heights the pass's CTA size and shared memory allow (ties to the taller tile).
+static int default_tile_y(int prec, int R, int ny, int kind) {
   int best = 0;
   long long best_rows = 0;
   for (int ty = 4; ty <= 64; ty += 4) {
-    if (!tile_ok(prec, R, ty)) continue;
+    if (!tile_ok(prec, R, ty, kind)) continue;
     const long long rows = (long long)(ty + 2 * R) * ((ny + ty - 1) / ty);
     if (best == 0 || rows <= best_rows) {
       best = ty;
@@ -325,10 +344,18 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
     memset(&h->opts, 0, sizeof(h->opts));
     return RSFD_OK;
   }
-  if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0)
+  if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0 || o->prefetch < 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
-  if (o->tile_y > 0 && !tile_ok(h->prec, h->R, o->tile_y))
+  if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_STORED)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: bad pass_kind");
+  if (o->prefetch > pass_max_depth())
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch must be <= " + std::to_string(pass_max_depth()));
+  const int kind = resolve_kind(h->prec, o->pass_kind);
+  if (o->tile_y > 0 && !tile_ok(h->prec, h->R, o->tile_y, kind))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: tile_y too large for this precision and stencil order");
+  if (o->prefetch > 0 && kind_smem(h->prec, h->R, o->tile_y > 0 ? o->tile_y : default_tile_y(h->prec, h->R, h->ny, kind),
+                                   o->prefetch, kind) > (size_t)(216 * 1024))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch depth does not fit in shared memory");
   if (o->iters_per_sync > kMaxHist)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: iters_per_sync must be <= " + std::to_string(kMaxHist));
   h->opts = *o;
@@ -380,16 +407,25 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.nb = h->nb;
   d.K = K;
   d.ncols = ncols;
-  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny);
-  if (!tile_ok(prec, h->R, d.tile_y)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
-  // deepest TMA prefetch that fits in shared memory: more planes in flight hide the load latency of a
-  // CTA that is alone on its SM
-  d.depth = 2;
-  for (int dp = pass_max_depth(); dp >= 2; --dp)
-    if (pass_smem(prec, h->R, d.tile_y, dp) <= (size_t)(216 * 1024)) {
-      d.depth = dp;
-      break;
-    }
+  d.kind = resolve_kind(prec, h->opts.pass_kind);
+  d.nvec = d.kind == RSFD_PASS_STORED ? 5 : 3;
+  d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind);
+  if (!tile_ok(prec, h->R, d.tile_y, d.kind)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
+  // TMA prefetch depth: the option, else the deepest that fits in shared memory (fused pass: a CTA
+  // alone on its SM) or 3 (stored-product pass: bundles are three times larger)
+  if (h->opts.prefetch > 0) {
+    d.depth = h->opts.prefetch;
+  } else {
+    d.depth = 1;
+    const int dmax = d.kind == RSFD_PASS_STORED ? 3 : pass_max_depth();
+    for (int dp = dmax; dp >= 1; --dp)
+      if (kind_smem(prec, h->R, d.tile_y, dp, d.kind) <= (size_t)(216 * 1024)) {
+        d.depth = dp;
+        break;
+      }
+  }
+  if (kind_smem(prec, h->R, d.tile_y, d.depth, d.kind) > (size_t)(216 * 1024))
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: prefetch depth does not fit in shared memory");
   d.tiles_x = (h->nx + pass_tile_x(h->R) - 1) / pass_tile_x(h->R);
   d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
   int W0 = h->opts.slots > 0 ? h->opts.slots : 256;
@@ -413,7 +449,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   {
     size_t freeb = 0, totb = 0;
     RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));
-    const size_t per_slot = 3 * (size_t)vec * vsz + 2 * (size_t)K * h->nb * vsz + (size_t)C * h->nb * hsz +
+    const size_t per_slot = (size_t)d.nvec * vec * vsz + 2 * (size_t)K * h->nb * vsz + (size_t)C * h->nb * hsz +
                             (size_t)K * C * sizeof(ShiftCoef) + (size_t)K * sizeof(ShiftState) +
                             (size_t)d.ctas_per_slot * 64 + 256;
     const size_t have = h->rbuf.bytes + h->xbuf.bytes + h->pbuf.bytes + h->rhist.bytes + h->coef.bytes;
@@ -427,7 +463,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
 
   // ---- workspace
   rsfd_status s;
-  if ((s = ensure(h, h->rbuf, (size_t)W * 3 * vec * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->rbuf, (size_t)W * d.nvec * vec * vsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->xbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->rhist, (size_t)W * C * h->nb * hsz)) != RSFD_OK) return s;
@@ -441,7 +477,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   if ((s = ensure(h, h->init_list, (size_t)W * 2 * sizeof(int))) != RSFD_OK) return s;
   if ((s = ensure(h, h->init_grid, (size_t)W * sizeof(long long))) != RSFD_OK) return s;
   if ((s = ensure(h, h->counters, 4 * sizeof(unsigned long long))) != RSFD_OK) return s;
-  if ((s = make_maps(h, W, d.tile_y)) != RSFD_OK) return s;
+  if ((s = make_maps(h, W, d.tile_y, d.kind)) != RSFD_OK) return s;
   SolverBuffers b;
   memset(&b, 0, sizeof(b));
   b.rbuf = h->rbuf.p;

@@ -105,13 +105,15 @@ struct SolveDims {
   int depth;          // TMA prefetch depth of the pass kernel
   int tiles_x, tiles_y, zchunk, nzchunks, ctas_per_slot;
   int ncols;
+  int kind;           // RSFD_PASS_RECOMPUTE or RSFD_PASS_STORED
+  int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
 };
 
 struct Handle;   // defined in rsfd_api.cu
 
 // Kernel launchers implemented in cocg_kernels.cu.
 struct SolverBuffers {
-  void* rbuf;             // [W][3][Nz][Ny][Nxp] vector elements
+  void* rbuf;             // [W][nvec][Nz][Ny][Nxp] vector elements
   void* xbuf;             // [W][K][nb] boundary rows of x^(i)
   void* pbuf;             // [W][K][nb] boundary rows of p^(i)
   void* rhist;            // [W][hist_len][nb] boundary rows of r_n (hi parts)
@@ -155,6 +157,11 @@ size_t vec_elem_bytes(int prec);
 size_t pot_elem_bytes(int prec);
 size_t hist_elem_bytes(int prec);
 size_t pass_smem(int prec, int R, int tile_y, int depth);
+size_t passu_smem(int prec, int R, int tile_y, int depth);
+int passu_threads(int R, int tile_y);
+int passu_max_threads(int prec);
+int passu_box_x();
+int passu_box_off();
 int pass_max_depth();
 int pass_box_x();
 int pass_box_off();

@@ -1,0 +1,59 @@
+"""Full-size parity: the 64x64x128 sampled-columns workload (4th order, 200 wells, 128 energies,
+eta = 1e-3) in the launch configuration bench.py times (double-float vectors, a batch of 32
+columns, automatic tile, slot and chunk choices), against stored oracle values.
+
+The stored values (tests/golden/sampled_columns_mixed_golden.npz) are the FP64 CPU oracle's G0_bb
+at tolerance 1e-10 on every 64th boundary row of the first columns of the workload, written by
+tests/golden/make_golden.py, which calls only oracle/.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from workloads import make_problem   # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sampled_columns_mixed_golden.npz")
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_00081_gb300.build_lib import build
+    build()
+    import paper_1502_00081_gb300 as m
+    m.load_library()
+    return m
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="stored oracle values not generated")
+def test_bench_batch_matches_stored_oracle(rs):
+    p = make_problem("sampled_columns_mixed")
+    g = np.load(GOLDEN)
+    gcols, rows, Go = g["cols"], g["rows"], g["G0"]          # Go: [K, nrows, ncols]
+    batch = p.cols[:32]
+    pos = [int(np.where(batch == c)[0][0]) for c in gcols]
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_DF64) as h:
+        brow = np.asarray(h.rows)
+        ridx = np.searchsorted(brow, rows)
+        assert np.array_equal(brow[ridx], rows)
+        G0 = torch.zeros((p.K, batch.size, h.nb), dtype=h.complex_dtype, device="cuda")
+        for tol, bound in ((p.tol, 2e-5), (1e-9, 1e-7)):
+            st, info, res = rs.rsfd_shifted_cocg(h.ptr, batch, p.energies, p.eta, tol, p.maxit, G0)
+            assert st == rs.RSFD_OK
+            G = G0.cpu().numpy()                                # [K, ncols, nb]
+            Gs = np.stack([G[:, j, :][:, ridx] for j in pos], axis=-1)   # [K, nrows, ncols]
+            err = np.linalg.norm(Gs - Go) / np.linalg.norm(Go)
+            print(f"tol {tol:g}: relative Frobenius error on the sampled rows {err:.3e}")
+            assert err <= bound, (tol, err)
+            # complex symmetry within the batch: G(row j_a, col j_b) = G(row j_b, col j_a)
+            idx = np.searchsorted(brow, batch)
+            S = G[:, :, idx]                                    # [K, col, row] over batch columns
+            sym = np.abs(S - S.transpose(0, 2, 1)).max() / np.abs(S).max()
+            assert sym <= 10 * bound, sym
