@@ -381,6 +381,101 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_shift_scaling(args):
+    """Shift-scaling experiment (the GPU analogue of the paper's Fig. 2, Sec. IV): seconds and seed
+    iterations of one shifted-COCG solve over K energies against K independent single-energy solves
+    (K = 1 reduces shifted COCG to COCG), on the workload's grid, for --ncols columns.  One JSON line
+    per (K, form)."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import make_problem
+    torch.cuda.set_device(0)
+    rs.load_library()
+    p = make_problem(args.workload)
+    prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[args.precision]
+    cols = p.cols[:args.ncols or 8]
+    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
+    G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+
+    def solve(E):
+        G = G0[:len(E)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, np.asarray(E), p.eta, p.tol, p.maxit, G)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st, info
+
+    solve(p.energies[:1])   # warm-up (graph capture, workspace)
+    for K in (1, 8, 32, 128):
+        E = p.energies[np.linspace(0, p.K - 1, K).round().astype(int)]
+        dt, st, info = solve(E)
+        print(json.dumps({"experiment": "shift_scaling", "form": "shifted", "K": K, "columns": int(cols.size),
+                          "seconds": dt, "status": int(st), "mean_seed_iterations": float(info["iters"].mean()),
+                          "mean_switches": float(info["switches"].mean()), "precision": args.precision}), flush=True)
+        if K <= args.max_independent:
+            tot, its = 0.0, []
+            for e in E:
+                dt1, st1, info1 = solve([e])
+                tot += dt1
+                its.append(float(info1["iters"].mean()))
+            print(json.dumps({"experiment": "shift_scaling", "form": "independent", "K": K, "columns": int(cols.size),
+                              "seconds": tot, "mean_iterations_per_energy": float(np.mean(its)),
+                              "total_iterations_per_column": float(np.sum(its)), "precision": args.precision}),
+                  flush=True)
+    h.close()
+
+
+def run_precision_speedup(args):
+    """Reduced-precision forms against the plain FP64 GPU form on the full pipeline (G0_bb for every
+    boundary column, Dyson, T), where the transmission can be compared: a 16x16x48 grid (h = 0.4,
+    4th order, 6 wells, two boundary planes per side), 16 energies in [0.3, 1.0] Ha, eta = 1e-3 and
+    1e-2.  Reports seconds, max |dT| and the G_bb error against the FP64 run, and the speedup where
+    |dT| <= 1e-4 and the G_bb error <= 1e-5 hold.  One JSON line per (eta, precision)."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import small_problem
+    torch.cuda.set_device(0)
+    rs.load_library()
+    for eta in (1e-3, 1e-2):
+        p = small_problem(grid=(16, 16, 48), h=0.4, fd_order=4, n_wells=6, n_energies=16, e_range=(0.3, 1.0),
+                          eta=eta, tol=1e-9, n_face=2, seed=17)
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+        ref = None
+        for name, prec in (("fp64", rs.RSFD_FP64), ("df64", rs.RSFD_DF64), ("mixed", rs.RSFD_MIXED)):
+            with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=2, precision=prec) as h:
+                cols = np.asarray(h.rows)
+                cdt = h.complex_dtype
+                G0 = torch.zeros((p.K, cols.size, h.nb), dtype=cdt, device="cuda")
+                SL = torch.from_numpy(SLh).cuda()
+                SR = torch.from_numpy(SRh).cuda()
+                G = torch.empty_like(G0)
+                times = []
+                for rep in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, p.tol, 200000, G0)
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
+                    T = rs.rsfd_transmission(h.ptr, G, SL, SR)
+                    torch.cuda.synchronize()
+                    times.append((time.perf_counter() - t0, t1 - t0))
+                Gh = G.cpu().numpy().astype(np.complex128)
+            tot, cocg = min(times)
+            line = {"experiment": "precision_speedup", "eta": eta, "precision": name, "status": int(st),
+                    "seconds": tot, "cocg_seconds": cocg, "columns": int(cols.size), "energies": p.K,
+                    "mean_seed_iterations": float(info["iters"].mean()), "T": [float(x) for x in T]}
+            if ref is None:
+                ref = (tot, np.asarray(T), Gh)
+            else:
+                dT = float(np.abs(np.asarray(T) - ref[1]).max())
+                gerr = float(np.linalg.norm(Gh - ref[2]) / np.linalg.norm(ref[2]))
+                ok = dT <= 1e-4 and gerr <= 1e-5
+                line.update({"max_abs_dT_vs_fp64": dT, "G_bb_rel_err_vs_fp64": gerr, "meets_tolerances": ok,
+                             "speedup_vs_fp64": (ref[0] / tot) if ok else None})
+            print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,7 +495,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--experiment", default=None, choices=[None, "shift_scaling", "precision_speedup"],
+                    help="run an experiment instead of the benchmark (JSON lines)")
+    ap.add_argument("--max-independent", type=int, default=32,
+                    help="shift_scaling: largest K also solved as K independent single-energy solves")
     args = ap.parse_args()
+    if args.experiment == "shift_scaling":
+        run_shift_scaling(args)
+        return
+    if args.experiment == "precision_speedup":
+        run_precision_speedup(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

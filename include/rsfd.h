@@ -102,7 +102,7 @@ typedef struct {
 
 /* Form of the seed iteration's pass (rsfd_solve_opts.pass_kind). */
 typedef enum {
-  RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED for RSFD_FP64 and RSFD_DF64, RSFD_PASS_RECOMPUTE for RSFD_MIXED */
+  RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED (measured faster in every precision on the 64^2 x 128 workload) */
   RSFD_PASS_RECOMPUTE = 1, /* three vectors per iteration (r_{n-1}, r_{n-2} in, r_n out); A r_{n-1} is
                               recomputed on the tile plus halo and A r_n again for the dot products */
   RSFD_PASS_STORED = 2     /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);
@@ -122,6 +122,7 @@ typedef struct {
                              (event nodes inside the CUDA graph); results in rsfd_get_stats */
   int32_t pass_kind;      /* rsfd_pass_kind */
   int32_t prefetch;       /* z-planes of input the pass keeps in flight (TMA), 1..7 */
+  int32_t rows_per_thread;/* RSFD_PASS_STORED: tile rows per thread, 1, 2 or 4 (tile_y must be a multiple) */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

@@ -55,7 +55,7 @@ class rsfd_col_info(ctypes.Structure):
 class rsfd_solve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32)]
+                ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32)]
 
 
 class rsfd_stats(ctypes.Structure):
@@ -185,10 +185,10 @@ def rsfd_boundary_rows(h):
 
 
 def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0,
-                           pass_kind=0, prefetch=0):
+                           pass_kind=0, prefetch=0, rows_per_thread=0):
     lib = load_library()
     o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile),
-                        int(pass_kind), int(prefetch))
+                        int(pass_kind), int(prefetch), int(rows_per_thread))
     _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
 
 

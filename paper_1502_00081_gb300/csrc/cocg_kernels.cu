@@ -588,7 +588,8 @@ __device__ __forceinline__ void block_sum_lane0(double (&v)[NV], double* s_red) 
 
 struct PassParams {
   SolveDims d;
-  void* rbuf;                // [W][3][Nz][Ny][Nxp] C
+  void* rbuf;                // [W][nvec][Nz][Ny][Nxp] C
+  const void* V;             // [Nz][Ny][Nxp] potential (VT)
   void* rhist;               // [W][hist_len][nb] H
   SlotState* slots;
   ShiftState* shifts;
@@ -856,7 +857,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
   typedef Pair<VT> PV;
   extern __shared__ unsigned char smem_raw[];
   __shared__ ScalarShared S;
-  __shared__ int s_last, s_abort;
+  __shared__ int s_last, s_abort[2];   // abort flags indexed by step parity (set before, read after a barrier)
   __shared__ __align__(8) unsigned long long bars[kMaxStages];
 
   const int slot = blockIdx.y;
@@ -955,7 +956,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    s_abort = 0;
+    s_abort[0] = s_abort[1] = 0;
   }
   __syncthreads();
   int issued = 0, s_fail = 0;
@@ -987,7 +988,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       issued = s + kDepth + 1;
     }
     if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
-      s_abort = 1;
+      s_abort[s & 1] = 1;
       atomicExch(p.error_flag, 1);
     }
     s_fail = s;
@@ -1034,7 +1035,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       SB[(size_t)isb * PEC + sidx] = rn;
     }
     __syncthreads();
-    if (s_abort) break;
+    if (s_abort[s & 1]) break;
     const int zo = c - R;
     if (s >= 3 * R && is_int && yin && zo >= z0 && zo < z1 && ina) {
       // A r_n on the output plane, then the three dot products
@@ -1076,7 +1077,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
     isb = (isb + 1 == NSB) ? 0 : isb + 1;
     isv = (isv + 1 == NSB) ? 0 : isv + 1;
   }
-  if (s_abort) {
+  if (s_abort[s_fail & 1]) {
     // drain the bundles still in flight (the one whose wait expired and those issued after it)
     // before the CTA's shared memory is released
     if (tid == 0) {
@@ -1100,27 +1101,62 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
 //   u_n = A r_n                                     (one stencil application per grid point)
 //
 // It moves five vectors per iteration (reads r_{n-1}, r_{n-2}, u_{n-1}; writes r_n, u_n) against
-// three for the fused pass, but applies the stencil once per point instead of on the tile plus
-// halo and again for the dots; in double-float arithmetic the stencil dominates, so this is the
-// faster form there.  Tile: 32 x TY points in x-y, one warp per tile row, plus halo warps that
-// evaluate r_n on the R-wide frame the stencil needs (the x-y box is 36 x (TY + 2R) points, TMA
-// loaded from x0 - 2).  Along z the r_n values of a thread's own column stay in registers.
+// three for the fused pass, but applies the stencil once per point instead of on the tile plus halo
+// and again for the dots; in double-float arithmetic the stencil dominates, so this is the faster
+// form there.
+//
+// CTA: a 32 x TY tile of one slot and a z-range.  Each tile thread owns one x column and P
+// consecutive rows, and keeps its r_n values of the last 2R + 1 planes in registers (the ring is
+// rotated by unrolling the z loop, so no register moves); frame warps evaluate r_n on the R-wide
+// frame the stencil needs, three points per thread.  Per z-plane one TMA bundle brings the
+// 36 x (TY + 2R) boxes of r_{n-1}, r_{n-2}, u_{n-1} (plane q); a step evaluates r_n on plane q, stores
+// it in a shared-memory ring of R + 1 planes, and evaluates A r_n on plane q - R, whose x and y
+// neighbours were stored in earlier steps (rows inside the thread's own P come from registers).  One
+// barrier per plane.
 constexpr int kUBoxX = 36;
 constexpr int kUBoxOff = 2;
-template <int MODE> struct MaxThreadsU { static constexpr int value = 704; };
+constexpr int kFramePts = 3;        // frame points per frame thread
+// launch bound per rows-per-thread P (one point per thread needs the most threads)
+template <int P> struct MaxThreadsU { static constexpr int value = 384; };
+template <> struct MaxThreadsU<1> { static constexpr int value = 640; };
 
-template <int MODE, int R>
-__global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassParams p,
-                                                                        const __grid_constant__ CUtensorMap tmR,
-                                                                        const __grid_constant__ CUtensorMap tmV) {
+__host__ __device__ __forceinline__ int passu_frame_warps(int R, int tile_y) {
+  const int nframe = 2 * R * tile_y + 2 * R * kTileX;
+  return (nframe + 32 * kFramePts - 1) / (32 * kFramePts);
+}
+// box coordinates of frame point h (R columns left and right of every tile row, then R rows below
+// and above the tile); cx = -1 past the last one
+template <int R>
+__device__ __forceinline__ void frame_point(int h, int TY, int nframe, int& cx, int& cy) {
+  cx = -1;
+  cy = 0;
+  if (h >= nframe) return;
+  if (h < 2 * R * TY) {
+    const int side = h / (R * TY), k = h - side * R * TY;
+    cy = k / R + R;
+    cx = side == 0 ? kUBoxOff - R + k % R : kUBoxOff + kTileX + k % R;
+  } else {
+    const int k2 = h - 2 * R * TY;
+    const int side = k2 / (R * kTileX), k = k2 - side * R * kTileX;
+    cx = kUBoxOff + k % kTileX;
+    cy = side == 0 ? k / kTileX : TY + R + k / kTileX;
+  }
+}
+
+template <typename VT> __device__ __forceinline__ VT zero_v() { return VT(); }
+template <> __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.f, 0.f); }
+
+template <int MODE, int R, int P>
+__global__ void __launch_bounds__(MaxThreadsU<P>::value) passu_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR) {
   typedef Ops<MODE> O;
   typedef Stencil<MODE, R> ST;
   typedef typename O::C C;
   typedef typename O::VT VT;
   typedef typename O::H H;
+  constexpr int Q = 2 * R + 1;
   extern __shared__ unsigned char smem_raw[];
   __shared__ ScalarShared S;
-  __shared__ int s_last, s_abort;
+  __shared__ int s_last, s_abort[2];   // abort flags indexed by step parity (set before, read after a barrier)
   __shared__ __align__(8) unsigned long long bars[kMaxStages];
 
   const int slot = blockIdx.y;
@@ -1132,7 +1168,7 @@ __global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassPar
   const int TY = d.tile_y;
   const int EY = TY + 2 * R;
   constexpr int BW = kUBoxX;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cta = blockIdx.x;
   const int tz = cta % d.nzchunks;
   const int txy = cta / d.nzchunks;
@@ -1140,45 +1176,20 @@ __global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassPar
   const int z0 = tz * d.zchunk;
   const int z1 = min(z0 + d.zchunk, d.nz);
   const int x0 = tx * kTileX, y0 = ty * TY;
-  const int nint = kTileX * TY;
-
-  // this thread's point in the box: a tile point (warp = tile row) or a frame point
-  const bool interior = tid < nint;
-  int cx = -1, cy = 0;
-  if (interior) {
-    cx = (tid & 31) + kUBoxOff;
-    cy = (tid >> 5) + R;
-  } else {
-    const int hh = tid - nint;
-    if (hh < 2 * R * TY) {                       // R columns left and right of every tile row
-      const int side = hh / (R * TY), k = hh - side * R * TY;
-      cy = k / R + R;
-      cx = side == 0 ? kUBoxOff - R + k % R : kUBoxOff + kTileX + k % R;
-    } else if (hh < 2 * R * TY + 2 * R * kTileX) {   // R rows below and above the tile
-      const int k2 = hh - 2 * R * TY;
-      const int side = k2 / (R * kTileX), k = k2 - side * R * kTileX;
-      cx = kUBoxOff + k % kTileX;
-      cy = side == 0 ? k / kTileX : TY + R + k / kTileX;
-    }
-  }
-  const bool has_pt = cx >= 0;
-  const int sidx = cy * BW + cx;
-  const int gx = x0 + (tid & 31), gy = y0 + (tid >> 5);
-  const bool own = interior && gx < d.nx && gy < d.ny;
+  const int NWI = TY / P;
+  const bool interior = warp < NWI;
+  const int row0 = warp * P;                 // first tile row of a tile thread
+  const int gx = x0 + lane;
   const long long plane_elems = (long long)d.nxp * d.ny;
 
-  // shared memory: per stage the boxes of r_{n-1}, r_{n-2}, u_{n-1} (plane q) and the tile of V
-  // (plane q - R); a ring of R + 2 planes of r_n
+  // shared memory: per stage the boxes of r_{n-1}, r_{n-2}, u_{n-1}; a ring of R + 1 planes of r_n
   const size_t PBb = (size_t)BW * EY * sizeof(C);
-  const size_t PVb = (size_t)kTileX * TY * sizeof(VT);
   const int PE = (int)(((PBb + 127) & ~(size_t)127) / sizeof(C));
-  const int PEV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(VT));
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   C* RA = (C*)base;
   C* RB = RA + (size_t)kStages * PE;
   C* UA = RB + (size_t)kStages * PE;
   C* SB = UA + (size_t)kStages * PE;
-  VT* VV = (VT*)(SB + (size_t)(R + 2) * PE);
 
   struct Coefs {
     typename O::Cplx a1, a2, aA;
@@ -1205,15 +1216,15 @@ __global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassPar
   const long long vec = (long long)d.nz * plane_elems;
   C* rout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + io) * vec;
   C* uout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + iuo) * vec;
+  const VT* Vg = reinterpret_cast<const VT*>(p.V);
   const typename O::Cplx a1 = sc.a1, a2 = sc.a2, aA = sc.aA;
   const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
   H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + sc.hc) * d.nb;
   const long long nxy = (long long)d.nx * d.ny;
 
   constexpr int mR = (MODE == RSFD_DF64) ? 4 : 2;
-  constexpr int mV = (MODE == RSFD_DF64) ? 2 : 1;
-  const int xr = mR * (x0 - kUBoxOff), xv = mV * x0, yb = y0 - R;
-  const uint32_t bundle_bytes = (uint32_t)(3 * PBb + PVb);
+  const int xr = mR * (x0 - kUBoxOff), yb = y0 - R;
+  const uint32_t bundle_bytes = (uint32_t)(3 * PBb);
   const int nsteps = (z1 - z0) + 2 * R;
   const int w1 = slot * 5 + i1, w2 = slot * 5 + i2, wu = slot * 5 + iu1;
 
@@ -1225,14 +1236,13 @@ __global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassPar
     tma_load_4d(smem_u32(RA + (size_t)k * PE), &tmR, xr, yb, q, w1, bar);
     tma_load_4d(smem_u32(RB + (size_t)k * PE), &tmR, xr, yb, q, w2, bar);
     tma_load_4d(smem_u32(UA + (size_t)k * PE), &tmR, xr, yb, q, wu, bar);
-    tma_load_3d(smem_u32(VV + (size_t)k * PEV), &tmV, xv, y0, q - R, bar);
   };
 
   if (tid == 0) {
     for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    s_abort = 0;
+    s_abort[0] = s_abort[1] = 0;
   }
   __syncthreads();
   int issued = 0, s_fail = 0;
@@ -1241,67 +1251,147 @@ __global__ void __launch_bounds__(MaxThreadsU<MODE>::value) passu_kernel(PassPar
     issued = min(kDepth, nsteps);
   }
 
-  C zq[2 * R + 1];   // r_n on planes c - R .. c + R of this thread's column
-#pragma unroll
-  for (int k = 0; k <= 2 * R; ++k) zq[k] = O::zero();
   typename AccOf<MODE>::type acc;
-  // ring positions: ist = s % kStages, par = (s / kStages) & 1, isw = s % (R + 2), isr = (s - R) % (R + 2)
-  int ist = 0, par = 0, isw = 0, isr = 2 % (R + 2);
-
-  for (int s = 0; s < nsteps; ++s) {
+  // Step s: r_n on plane q = z0 - R + s (TMA stage ist, shared ring slot s % (R + 1)) and, from step
+  // 2R on, A r_n on plane c = q - R (ring slot (s - R) % (R + 1) = (s + 1) % (R + 1)).
+  int ist = 0, par = 0, isw = 0, s = 0;
+  auto begin_step = [&]() {
     if (tid == 0 && s + kDepth < nsteps) {
       issue(s + kDepth);
       issued = s + kDepth + 1;
     }
     if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
-      s_abort = 1;
+      s_abort[s & 1] = 1;
       atomicExch(p.error_flag, 1);
     }
     s_fail = s;
-    // r_n on plane q = z0 - R + s at this thread's point (zero outside the grid: TMA zero fill)
-    C rq = O::zero();
-    VT vc = VT();
-    if (has_pt) {
-      const size_t o = (size_t)ist * PE + sidx;
-      rq = ST::combine(a1, RA[o], a2, RB[o], aA, UA[o]);                     // Eq. rvec
-      SB[(size_t)isw * PE + sidx] = rq;
-    }
-    if (interior) {
-#pragma unroll
-      for (int k = 0; k < 2 * R; ++k) zq[k] = zq[k + 1];
-      zq[2 * R] = rq;
-      vc = VV[(size_t)ist * PEV + tid];
-    }
+  };
+  auto end_step = [&]() -> bool {
     __syncthreads();
-    if (s_abort) break;
-    const int c = z0 - 2 * R + s;      // plane of this step's u_n = A r_n
-    if (own && s >= 2 * R) {
-      const C* P = SB + (size_t)isr * PE;
-      const C n1[6] = {zq[R - 1], zq[R + 1], P[sidx - 1], P[sidx + 1], P[sidx - BW], P[sidx + BW]};
-      C n2[6];
-      if (R == 2) {
-        n2[0] = zq[0]; n2[1] = zq[2 * R]; n2[2] = P[sidx - 2]; n2[3] = P[sidx + 2];
-        n2[4] = P[sidx - 2 * BW]; n2[5] = P[sidx + 2 * BW];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) n2[k] = O::zero();
-      }
-      const C rc = zq[R];
-      const C u = ST::applyA(rc, n1, n2, vc, zre, zim, mh1, mh2);
-      acc.add(rc, u);
-      const size_t g = (size_t)c * plane_elems + (size_t)gy * d.nxp + gx;
-      rout[g] = rc;
-      uout[g] = u;
-      int pl = -1;
-      if (c < d.nface) pl = c;
-      else if (c >= d.nz - d.nface) pl = c - d.nz + 2 * d.nface;
-      if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gy * d.nx + gx] = O::hi(rc);
-    }
+    if (s_abort[s & 1]) return false;
     if (++ist == kStages) { ist = 0; par ^= 1; }
-    isw = (isw + 1 == R + 2) ? 0 : isw + 1;
-    isr = (isr + 1 == R + 2) ? 0 : isr + 1;
+    isw = (isw == R) ? 0 : isw + 1;
+    ++s;
+    return true;
+  };
+  bool ok = true;
+  if (interior) {
+    C zq[P][Q];   // zq[k][t % Q]: r_n of row row0 + k on the plane combined in step t
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+#pragma unroll
+      for (int t = 0; t < Q; ++t) zq[k][t] = O::zero();
+    bool own[P];
+    int gyk[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      gyk[k] = y0 + row0 + k;
+      own[k] = gx < d.nx && gyk[k] < d.ny;
+    }
+    // the combine of plane q for the P rows; the result enters ring slot isw and zq[.][PH]
+    auto combine_rows = [&](auto ph_c) {
+      constexpr int PH = decltype(ph_c)::value;
+      C* sw = SB + (size_t)isw * PE;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int o = (row0 + k + R) * BW + lane + kUBoxOff;
+        const size_t os = (size_t)ist * PE + o;
+        const C rq = ST::combine(a1, RA[os], a2, RB[os], aA, UA[os]);   // Eq. rvec
+        sw[o] = rq;
+        zq[k][PH] = rq;
+      }
+    };
+    // prologue: planes z0 - R .. z0 + R - 1, the combine only
+#pragma unroll
+    for (int t = 0; t < 2 * R; ++t) {
+      if (ok && s < nsteps) {
+        begin_step();
+        if (t == 0) combine_rows(std::integral_constant<int, 0>());
+        if (t == 1) combine_rows(std::integral_constant<int, 1 % Q>());
+        if (t == 2) combine_rows(std::integral_constant<int, 2 % Q>());
+        if (t == 3) combine_rows(std::integral_constant<int, 3 % Q>());
+        ok = end_step();
+      }
+    }
+    // steady state: step s = 2R + g Q + j has ring phase (2R + j) % Q
+    auto steady = [&](auto j_c) {
+      constexpr int PH = (2 * R + decltype(j_c)::value) % Q;       // slot of plane q
+      constexpr int CC = (PH + Q - R) % Q;                         // slot of plane c = q - R
+      begin_step();
+      combine_rows(std::integral_constant<int, PH>());
+      const int c = z0 - 2 * R + s;
+      const C* P0 = SB + (size_t)((isw + 1 == R + 1) ? 0 : isw + 1) * PE;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int o = (row0 + k + R) * BW + lane + kUBoxOff;
+        const C rc = zq[k][CC];
+        C n1[6], n2[6];
+        n1[0] = zq[k][(CC + Q - 1) % Q];
+        n1[1] = zq[k][(CC + 1) % Q];
+        n1[2] = P0[o - 1];
+        n1[3] = P0[o + 1];
+        n1[4] = (k >= 1) ? zq[k - 1 >= 0 ? k - 1 : 0][CC] : P0[o - BW];
+        n1[5] = (k + 1 < P) ? zq[k + 1 < P ? k + 1 : 0][CC] : P0[o + BW];
+        if (R == 2) {
+          n2[0] = zq[k][(CC + Q - 2) % Q];
+          n2[1] = zq[k][(CC + 2) % Q];
+          n2[2] = P0[o - 2];
+          n2[3] = P0[o + 2];
+          n2[4] = (k >= 2) ? zq[k - 2 >= 0 ? k - 2 : 0][CC] : P0[o - 2 * BW];
+          n2[5] = (k + 2 < P) ? zq[k + 2 < P ? k + 2 : 0][CC] : P0[o + 2 * BW];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 6; ++m) n2[m] = O::zero();
+        }
+        const long long gidx = (long long)c * plane_elems + (long long)gyk[k] * d.nxp + gx;
+        const VT v = own[k] ? Vg[gidx] : zero_v<VT>();
+        const C u = ST::applyA(rc, n1, n2, v, zre, zim, mh1, mh2);
+        if (own[k]) {
+          acc.add(rc, u);
+          rout[gidx] = rc;
+          uout[gidx] = u;
+          int pl = -1;
+          if (c < d.nface) pl = c;
+          else if (c >= d.nz - d.nface) pl = c - d.nz + 2 * d.nface;
+          if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gyk[k] * d.nx + gx] = O::hi(rc);
+        }
+      }
+      ok = end_step();
+    };
+    while (ok && s < nsteps) {
+      steady(std::integral_constant<int, 0>());
+      if (ok && s < nsteps) steady(std::integral_constant<int, 1>());
+      if (ok && s < nsteps) steady(std::integral_constant<int, 2>());
+      if (R == 2) {
+        if (ok && s < nsteps) steady(std::integral_constant<int, 3>());
+        if (ok && s < nsteps) steady(std::integral_constant<int, 4>());
+      }
+    }
+  } else {
+    const int nframe = 2 * R * TY + 2 * R * kTileX;
+    const int FT = passu_frame_warps(R, TY) * 32;
+    int fo[kFramePts];
+    bool fv[kFramePts];
+#pragma unroll
+    for (int j = 0; j < kFramePts; ++j) {
+      int cx, cy;
+      frame_point<R>((warp - NWI) * 32 + lane + j * FT, TY, nframe, cx, cy);
+      fv[j] = cx >= 0;
+      fo[j] = fv[j] ? cy * BW + cx : 0;
+    }
+    while (ok && s < nsteps) {
+      begin_step();
+      C* sw = SB + (size_t)isw * PE;
+#pragma unroll
+      for (int j = 0; j < kFramePts; ++j) {
+        const size_t os = (size_t)ist * PE + fo[j];
+        const C r = ST::combine(a1, RA[os], a2, RB[os], aA, UA[os]);
+        if (fv[j]) sw[fo[j]] = r;
+      }
+      ok = end_step();
+    }
   }
-  if (s_abort) {
+  if (!ok) {
     // drain the bundles still in flight (the one whose wait expired and those issued after it)
     // before the CTA's shared memory is released
     if (tid == 0) {
@@ -1521,6 +1611,7 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   PassParams p;
   p.d = d;
   p.rbuf = b.rbuf;
+  p.V = b.V;
   p.rhist = b.rhist;
   p.slots = b.slots;
   p.shifts = b.shifts;
@@ -1541,7 +1632,10 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   dim3 grid(d.ctas_per_slot, d.W);
   if (d.kind == RSFD_PASS_STORED) {
     const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth);
-    passu_kernel<MODE, R><<<grid, passu_threads(R, d.tile_y), smem, st>>>(p, *b.tmR, *b.tmV);
+    const int thr = passu_threads(d.rows, R, d.tile_y);
+    if (d.rows == 1) passu_kernel<MODE, R, 1><<<grid, thr, smem, st>>>(p, *b.tmR);
+    else if (d.rows == 2) passu_kernel<MODE, R, 2><<<grid, thr, smem, st>>>(p, *b.tmR);
+    else passu_kernel<MODE, R, 4><<<grid, thr, smem, st>>>(p, *b.tmR);
   } else {
     const size_t smem = pass_smem(MODE, R, d.tile_y, d.depth);
     pass_kernel<MODE, R><<<grid, pass_threads(R, d.tile_y), smem, st>>>(p, *b.tmR, *b.tmV);
@@ -1565,19 +1659,18 @@ size_t pass_smem(int prec, int R, int tile_y, int depth) {
 int pass_max_depth() { return kMaxDepth; }
 int passu_box_x() { return kUBoxX; }
 int passu_box_off() { return kUBoxOff; }
-// tile rows (one warp each) plus the warps of the R-wide frame: 2 R TY + 2 R 32 points
-int passu_threads(int R, int tile_y) { return 32 * tile_y + (2 * R * tile_y + 2 * R * kTileX + 31) / 32 * 32; }
-size_t passu_smem(int prec, int R, int tile_y, int depth) {
-  const size_t es = prec == RSFD_MIXED ? 8 : 16, vs = prec == RSFD_MIXED ? 4 : 8;
-  const size_t pb = ((size_t)kUBoxX * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
-  const size_t pv = ((size_t)kTileX * tile_y * vs + 127) & ~(size_t)127;
-  const size_t stages = (size_t)depth + 1;
-  return stages * (3 * pb + pv) + (size_t)(R + 2) * pb + 128;
+// tile threads (one x column and P rows each) plus the frame warps
+int passu_threads(int rows, int R, int tile_y) {
+  return 32 * (tile_y / rows) + 32 * passu_frame_warps(R, tile_y);
 }
-int passu_max_threads(int prec) {
-  if (prec == RSFD_DF64) return MaxThreadsU<RSFD_DF64>::value;
-  if (prec == RSFD_FP64) return MaxThreadsU<RSFD_FP64>::value;
-  return MaxThreadsU<RSFD_MIXED>::value;
+int passu_max_threads(int rows) {
+  return rows == 1 ? MaxThreadsU<1>::value : rows == 2 ? MaxThreadsU<2>::value : MaxThreadsU<4>::value;
+}
+size_t passu_smem(int prec, int R, int tile_y, int depth) {
+  const size_t es = prec == RSFD_MIXED ? 8 : 16;
+  const size_t pb = ((size_t)kUBoxX * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
+  const size_t stages = (size_t)depth + 1;
+  return stages * 3 * pb + (size_t)(R + 1) * pb + 128;
 }
 int pass_max_threads(int prec) {
   if (prec == RSFD_DF64) return MaxThreads<RSFD_DF64>::value;
@@ -1590,7 +1683,9 @@ cudaError_t kernels_init() {
   cudaError_t e = cudaSuccess;
 #define RSFD_ATTR(M, R)                                                                                  \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(pass_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(passu_kernel<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(passu_kernel<M, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(passu_kernel<M, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(passu_kernel<M, R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   RSFD_ATTR(RSFD_FP64, 1)
   RSFD_ATTR(RSFD_FP64, 2)
   RSFD_ATTR(RSFD_MIXED, 1)

@@ -107,6 +107,7 @@ struct SolveDims {
   int ncols;
   int kind;           // RSFD_PASS_RECOMPUTE or RSFD_PASS_STORED
   int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
+  int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
 };
 
 struct Handle;   // defined in rsfd_api.cu
@@ -114,6 +115,7 @@ struct Handle;   // defined in rsfd_api.cu
 // Kernel launchers implemented in cocg_kernels.cu.
 struct SolverBuffers {
   void* rbuf;             // [W][nvec][Nz][Ny][Nxp] vector elements
+  const void* V;          // [Nz][Ny][Nxp] potential
   void* xbuf;             // [W][K][nb] boundary rows of x^(i)
   void* pbuf;             // [W][K][nb] boundary rows of p^(i)
   void* rhist;            // [W][hist_len][nb] boundary rows of r_n (hi parts)
@@ -158,8 +160,8 @@ size_t pot_elem_bytes(int prec);
 size_t hist_elem_bytes(int prec);
 size_t pass_smem(int prec, int R, int tile_y, int depth);
 size_t passu_smem(int prec, int R, int tile_y, int depth);
-int passu_threads(int R, int tile_y);
-int passu_max_threads(int prec);
+int passu_threads(int rows, int R, int tile_y);
+int passu_max_threads(int rows);
 int passu_box_x();
 int passu_box_off();
 int pass_max_depth();

@@ -4,7 +4,8 @@ This script calls only ``oracle/`` (and the seeded inputs of ``workloads``); not
 comes from the CUDA library.  Output, for the 64x64x128 "sampled_columns_mixed" workload:
 
 * ``sampled_columns_mixed_golden.npz``: for the first ``--ncols`` columns of the workload, the
-  oracle's G0_bb (tol 1e-10, FP64) on every 64th boundary row and every energy.
+  oracle's G0_bb (tol 1e-10, FP64) on every 64th boundary row and every energy, and the same at the
+  workload's own tolerance (``G0_loose``).
 * ``sampled_columns_mixed_oracle_iterations.json``: the oracle's seed iterations per column at the
   workload's own tolerance (used to scale the bounded CPU-baseline sample in bench.py).
 
@@ -60,7 +61,9 @@ def main():
     np.savez_compressed(os.path.join(HERE, f"{args.workload}_golden.npz"),
                         cols=np.array(cols), rows=rows, row_stride=args.row_stride,
                         G0=np.stack([o[1] for o in tight], axis=-1),        # [K, nrows, ncols]
-                        iterations=np.array([o[2] for o in tight]), tol=1e-10)
+                        iterations=np.array([o[2] for o in tight]), tol=1e-10,
+                        G0_loose=np.stack([o[1] for o in loose], axis=-1),  # the oracle at the workload's tol
+                        tol_loose=p.tol)
     json.dump({"workload": args.workload, "tol": p.tol, "columns": cols,
                "iterations": [int(o[2]) for o in loose], "switches": [int(o[3]) for o in loose],
                "status": [int(o[4]) for o in loose], "seconds": [round(o[5], 1) for o in loose],

@@ -178,3 +178,22 @@ def test_argument_errors(rs):
             args.update(bad)
             with pytest.raises(rs.RsfdError):
                 rs.rsfd_shifted_cocg(h.ptr, args["cols"], p.energies, args["eta"], args["tol"], 100, G0)
+        # launch options the pass cannot honour are rejected before any launch
+        for bad in (dict(pass_kind=3), dict(rows_per_thread=3), dict(prefetch=8), dict(pass_kind=2, tile_y=6,
+                                                                                   rows_per_thread=4),
+                    dict(pass_kind=2, tile_y=64)):
+            with pytest.raises(rs.RsfdError):
+                rs.rsfd_set_solve_options(h.ptr, **bad)
+
+
+@pytest.mark.parametrize("rows,tile_y", [(1, 8), (2, 12), (4, 8)])
+def test_stored_pass_rows_per_thread(rs, rows, tile_y):
+    """Every thread organisation of the stored-product pass (tile rows per thread, ragged tiles in x,
+    y and z) gives the oracle's G0 in FP64."""
+    p = small_problem(grid=(37, 26, 19), h=0.45, fd_order=4, n_wells=4, n_energies=5, e_range=(0.3, 2.5),
+                      eta=5e-2, tol=1e-12, cols=5)
+    st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_FP64, opts=dict(pass_kind=2, rows_per_thread=rows, tile_y=tile_y,
+                                                                  slots=3, z_chunk=7))
+    assert st == rs.RSFD_OK
+    Go, _ = shifted_cocg_columns(p)
+    assert relf(G, Go) <= 1e-9
