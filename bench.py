@@ -407,7 +407,8 @@ def run_shift_scaling(args):
 
     solve(p.energies[:1])   # warm-up (graph capture, workspace)
     for K in (1, 8, 32, 128):
-        E = p.energies[np.linspace(0, p.K - 1, K).round().astype(int)]
+        idx = np.linspace(0, p.K - 1, K).round().astype(int) if K > 1 else np.array([p.K // 2])
+        E = p.energies[idx]
         dt, st, info = solve(E)
         print(json.dumps({"experiment": "shift_scaling", "form": "shifted", "K": K, "columns": int(cols.size),
                           "seconds": dt, "status": int(st), "mean_seed_iterations": float(info["iters"].mean()),
@@ -429,51 +430,55 @@ def run_precision_speedup(args):
     """Reduced-precision forms against the plain FP64 GPU form on the full pipeline (G0_bb for every
     boundary column, Dyson, T), where the transmission can be compared: a 16x16x48 grid (h = 0.4,
     4th order, 6 wells, two boundary planes per side), 16 energies in [0.3, 1.0] Ha, eta = 1e-3 and
-    1e-2.  Reports seconds, max |dT| and the G_bb error against the FP64 run, and the speedup where
-    |dT| <= 1e-4 and the G_bb error <= 1e-5 hold.  One JSON line per (eta, precision)."""
+    1e-2.  Every form runs at the same stopping tolerance (1e-6); accuracy is judged against an FP64
+    run at tol 1e-10, and the speedup over the FP64 form at tol 1e-6 is reported where |dT| <= 1e-4
+    and the G_bb error <= 1e-5 hold.  One JSON line per (eta, precision)."""
     import torch
     import paper_1502_00081_gb300 as rs
     from workloads import small_problem
     torch.cuda.set_device(0)
     rs.load_library()
+    tol = 1e-6
     for eta in (1e-3, 1e-2):
         p = small_problem(grid=(16, 16, 48), h=0.4, fd_order=4, n_wells=6, n_energies=16, e_range=(0.3, 1.0),
-                          eta=eta, tol=1e-9, n_face=2, seed=17)
+                          eta=eta, tol=tol, n_face=2, seed=17)
         SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
-        ref = None
-        for name, prec in (("fp64", rs.RSFD_FP64), ("df64", rs.RSFD_DF64), ("mixed", rs.RSFD_MIXED)):
+
+        def run(prec, tol_run, maxit, reps):
             with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=2, precision=prec) as h:
                 cols = np.asarray(h.rows)
-                cdt = h.complex_dtype
-                G0 = torch.zeros((p.K, cols.size, h.nb), dtype=cdt, device="cuda")
-                SL = torch.from_numpy(SLh).cuda()
-                SR = torch.from_numpy(SRh).cuda()
+                G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+                SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
                 G = torch.empty_like(G0)
-                times = []
-                for rep in range(2):
+                best = None
+                for rep in range(reps):
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, p.tol, 200000, G0)
+                    st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, tol_run, maxit, G0)
                     torch.cuda.synchronize()
                     t1 = time.perf_counter()
                     rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
                     T = rs.rsfd_transmission(h.ptr, G, SL, SR)
                     torch.cuda.synchronize()
-                    times.append((time.perf_counter() - t0, t1 - t0))
-                Gh = G.cpu().numpy().astype(np.complex128)
-            tot, cocg = min(times)
-            line = {"experiment": "precision_speedup", "eta": eta, "precision": name, "status": int(st),
-                    "seconds": tot, "cocg_seconds": cocg, "columns": int(cols.size), "energies": p.K,
-                    "mean_seed_iterations": float(info["iters"].mean()), "T": [float(x) for x in T]}
-            if ref is None:
-                ref = (tot, np.asarray(T), Gh)
-            else:
-                dT = float(np.abs(np.asarray(T) - ref[1]).max())
-                gerr = float(np.linalg.norm(Gh - ref[2]) / np.linalg.norm(ref[2]))
-                ok = dT <= 1e-4 and gerr <= 1e-5
-                line.update({"max_abs_dT_vs_fp64": dT, "G_bb_rel_err_vs_fp64": gerr, "meets_tolerances": ok,
-                             "speedup_vs_fp64": (ref[0] / tot) if ok else None})
-            print(json.dumps(line), flush=True)
+                    t = (time.perf_counter() - t0, t1 - t0)
+                    best = t if best is None or t[0] < best[0] else best
+                return best, int(st), float(info["iters"].mean()), np.asarray(T), G.cpu().numpy().astype(np.complex128)
+
+        _, _, _, T_ref, G_ref = run(rs.RSFD_FP64, 1e-10, 200000, 1)
+        base = None
+        for name, prec in (("fp64", rs.RSFD_FP64), ("df64", rs.RSFD_DF64), ("mixed", rs.RSFD_MIXED)):
+            (tot, cocg), st, its, T, G = run(prec, tol, 20000, 2)
+            dT = float(np.abs(T - T_ref).max())
+            gerr = float(np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref))
+            ok = st == 0 and dT <= 1e-4 and gerr <= 1e-5
+            if name == "fp64":
+                base = tot
+            print(json.dumps({"experiment": "precision_speedup", "eta": eta, "precision": name, "tol": tol,
+                              "status": st, "seconds": tot, "cocg_seconds": cocg, "columns": int(G.shape[1]),
+                              "energies": p.K, "mean_seed_iterations": its, "max_abs_dT": dT,
+                              "G_bb_rel_err": gerr, "reference": "FP64 GPU form at tol 1e-10",
+                              "meets_tolerances": ok,
+                              "speedup_vs_fp64": (base / tot) if ok and base else None}), flush=True)
 
 
 def main():

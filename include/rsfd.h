@@ -159,6 +159,20 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double h, int32
  * be NULL (size query) or a host array of at least *nb entries. */
 rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows);
 
+/* Interior planes whose rows the solver records next to b, for the diagonal blocks G_T(z_l, z_l)
+ * that the density of states needs (Sec. III B, discussion after Eq. sec3-06).  After this call
+ * rsfd_shifted_cocg writes, for every column, the nr = nb + n*Nx*Ny recorded rows: b first, then
+ * plane z[0], ..., plane z[n-1] (each plane in x-fastest order; rsfd_tracked_rows lists them).
+ *   n  0 <= n <= RSFD_MAX_TRACKED_PLANES (0 restores nr = nb).
+ *   z  host [n] distinct interior planes, n_face <= z[i] < Nz - n_face.
+ * RSFD_ERR_ARG otherwise (the previous setting is kept). */
+#define RSFD_MAX_TRACKED_PLANES 16
+rsfd_status rsfd_set_tracked_planes(rsfd_handle h, int32_t n, const int32_t* z);
+
+/* The recorded row set (b, then the tracked planes); *nr receives its size, rows may be NULL
+ * (size query) or a host array of at least *nr entries. */
+rsfd_status rsfd_tracked_rows(rsfd_handle h, int32_t* nr, int64_t* rows);
+
 /* Set launch options for later solves (NULL restores the defaults). */
 rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* opts);
 
@@ -170,7 +184,8 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* opts);
  *   tol        convergence threshold on ||r^(k)||_2 / ||e_j||_2 for every k.
  *   maxit      iteration cap per column (>= 1).
  *   seed_kind  rsfd_seed_kind; seed_index used with RSFD_SEED_INDEX.
- *   G0_bb      device output [K][ncols][nb], c64 or c128 per the handle's precision.
+ *   G0_bb      device output [K][ncols][nr], c64 or c128 per the handle's precision; nr = nb unless
+ *              interior planes are tracked (rsfd_set_tracked_planes).
  *   info       host output [ncols] (nullable).
  *   final_res  host output [ncols][K] residual of each energy at exit (nullable).
  * Synchronises the handle's stream.  Returns RSFD_OK when every column
@@ -193,6 +208,20 @@ rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out);
  *   refine_residual  host [K] (nullable): ||G0 - M G||_F / ||G0||_F after refinement. */
 rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
                                 int32_t K, void* G_bb, double* refine_residual);
+
+/* Dyson step on the recorded row set (Eq. sec3-01a with Sigma supported on b; the interior blocks
+ * G_T(z_0, z_l), G_T(z_l, z_l) of Sec. III B):
+ *   G(k) = G0(k) + G0(k)[:, b] Sigma_bb(k) (I - G0_bb(k) Sigma_bb(k))^{-1} G0(k)[b, :].
+ * G0 must come from a solve whose columns are the recorded rows in rsfd_tracked_rows order
+ * (ncols = nr).  G[b, b] equals rsfd_dyson_boundary's G_bb; G[l, l] is the perturbed diagonal block of
+ * tracked plane l, whose -Im trace / pi gives the plane's density of states.  LU with partial pivoting
+ * and two FP64 refinement steps, as rsfd_dyson_boundary.
+ *   G0       device [K][nr][nr] (handle precision), column-major per energy.
+ *   Sigma_L, Sigma_R  device [K][ns][ns] c128.
+ *   G        device output, same layout and type as G0 (may not alias G0).
+ *   refine_residual  host [K] (nullable): ||G0_b: - M G_b:||_F / ||G0_b:||_F on the boundary rows. */
+rsfd_status rsfd_dyson_tracked(rsfd_handle h, const void* G0, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                               void* G, double* refine_residual);
 
 /* Fisher-Lee transmission (Eq. TF; Gamma = i(Sigma - Sigma^dag)):
  *   T(k) = Tr[Gamma_L G_RL^dag Gamma_R G_RL],  G_RL = G_bb(k)[right slab, left slab].

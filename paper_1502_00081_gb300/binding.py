@@ -73,6 +73,8 @@ _SIGNATURES = {
                                    ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(rsfd_projectors), ctypes.c_int32, _P]),
     "rsfd_boundary_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    "rsfd_set_tracked_planes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "rsfd_tracked_rows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     "rsfd_set_solve_options": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_solve_opts)]),
     "rsfd_shifted_cocg": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
@@ -80,6 +82,7 @@ _SIGNATURES = {
                                          ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
     "rsfd_dyson_boundary": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_dyson_tracked": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_transmission": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_lead_sigma_uniform": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int32,
@@ -173,6 +176,36 @@ def rsfd_create(grid, h, fd_order, V_loc, n_face=0, proj=None, precision=RSFD_FP
                          _stream_ptr(stream))
     _check(None, st)
     return out
+
+
+def rsfd_set_tracked_planes(h, planes):
+    lib = load_library()
+    z = np.ascontiguousarray(np.asarray(planes, dtype=np.int32).ravel())
+    _check(h, lib.rsfd_set_tracked_planes(h, int(z.size), z.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+                                          if z.size else None))
+
+
+def rsfd_tracked_rows(h):
+    lib = load_library()
+    nr = ctypes.c_int32()
+    _check(h, lib.rsfd_tracked_rows(h, ctypes.byref(nr), None))
+    rows = np.zeros(nr.value, np.int64)
+    _check(h, lib.rsfd_tracked_rows(h, ctypes.byref(nr), rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return rows
+
+
+def rsfd_dyson_tracked(h, G0, Sigma_L, Sigma_R, G):
+    """Dyson step on the recorded rows (G0, G: [K][nr][nr] column-major); returns refinement residuals."""
+    import torch
+    lib = load_library()
+    K = int(G0.shape[0])
+    p0 = _dev_ptr(G0, (torch.complex64, torch.complex128), name="G0")
+    pl = _dev_ptr(Sigma_L, (torch.complex128,), name="Sigma_L")
+    pr = _dev_ptr(Sigma_R, (torch.complex128,), name="Sigma_R")
+    pg = _dev_ptr(G, (G0.dtype,), tuple(G0.shape), name="G")
+    ref = np.zeros(K, np.float64)
+    _check(h, lib.rsfd_dyson_tracked(h, p0, pl, pr, K, pg, ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return ref
 
 
 def rsfd_boundary_rows(h):

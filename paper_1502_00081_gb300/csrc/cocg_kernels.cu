@@ -515,6 +515,18 @@ template <int MODE> struct AccOf { typedef AccDF type; };
 template <> struct AccOf<RSFD_MIXED> { typedef AccK type; };
 template <> struct AccOf<RSFD_FP64> { typedef Acc<double> type; };
 
+// index of plane z among the recorded planes (boundary planes, then the tracked interior planes),
+// -1 when its rows are not recorded
+__device__ __forceinline__ int recorded_plane(const SolveDims& d, int z) {
+  if (z < d.nface) return z;
+  if (z >= d.nz - d.nface) return z - d.nz + 2 * d.nface;
+  int pl = -1;
+#pragma unroll 4
+  for (int e = 0; e < d.ntrack; ++e)
+    if (d.track[e] == z) pl = 2 * d.nface + e;
+  return pl;
+}
+
 // ------------------------------------------------------------------------------------------------
 // mbarrier / TMA primitives (inline PTX)
 // ------------------------------------------------------------------------------------------------
@@ -1057,9 +1069,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       const C va = ST::applyA(cq.a, n1a, n2a, vq[R].a, zre, zim, mh1, mh2);
       acc.add(cq.a, va);
       C* dst = rout + (size_t)zo * plane_elems + (size_t)gy * d.nxp + gxa;
-      int pl = -1;
-      if (zo < d.nface) pl = zo;
-      else if (zo >= d.nz - d.nface) pl = zo - d.nz + 2 * d.nface;
+      const int pl = recorded_plane(d, zo);
       H* hrow = hist + (size_t)pl * nxy + (size_t)gy * d.nx + gxa;
       if (inb) {
         const C vb = ST::applyA(cq.b, n1b, n2b, vq[R].b, zre, zim, mh1, mh2);
@@ -1350,9 +1360,7 @@ __global__ void __launch_bounds__(MaxThreadsU<P>::value) passu_kernel(PassParams
           acc.add(rc, u);
           rout[gidx] = rc;
           uout[gidx] = u;
-          int pl = -1;
-          if (c < d.nface) pl = c;
-          else if (c >= d.nz - d.nface) pl = c - d.nz + 2 * d.nface;
+          const int pl = recorded_plane(d, c);
           if (pl >= 0) hist[(size_t)pl * nxy + (size_t)gyk[k] * d.nx + gx] = O::hi(rc);
         }
       }

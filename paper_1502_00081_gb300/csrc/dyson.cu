@@ -257,6 +257,17 @@ __global__ void trace_prod_batched(const double2* GL, const double2* W, int ns, 
   }
 }
 
+// dst[b][c][0:nrow] = src[b][c][0:nrow] for ncol columns: the leading rows of a column-major block
+__global__ void copy_rows_c128(const double2* src, int lds, double2* dst, int ldd, int nrow, int ncol, int batch) {
+  const long long per = (long long)nrow * ncol;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per * batch;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, e = t - b * per;
+    const long long c = e / nrow, i = e - c * nrow;
+    dst[(b * ncol + c) * ldd + i] = src[(b * ncol + c) * lds + i];
+  }
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
@@ -340,6 +351,88 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
     if (hinfo[k] != 0)
       return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_dyson_boundary: singular I - G0 Sigma at energy " + std::to_string(k));
   (void)zero;
+  return RSFD_OK;
+}
+
+// Dyson step on the recorded rows: G = G0 + G0[:, b] Sigma Y with Y = (I - G0_bb Sigma)^{-1} G0[b, :]
+// (the boundary rows of G), all nr x nr per energy, column-major.
+rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL, const void* SR, int K, void* G,
+                              double* refres) {
+  const int nb = handle_nb(h);
+  const int ns = nb / 2;
+  const long long r2 = (long long)nr * nr, b2 = (long long)nb * nb, bn = (long long)nb * nr;
+  const bool fp64 = handle_prec(h) != RSFD_MIXED;
+  rsfd_status s;
+  void *pG0, *pM, *pLU, *pY, *pR, *pPiv, *pRed, *pW;
+  if ((s = handle_ensure(h, 0, r2 * K * sizeof(double2), &pG0)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 1, b2 * K * sizeof(double2), &pM)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, b2 * K * sizeof(double2), &pLU)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 3, bn * K * sizeof(double2), &pY)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, bn * K * sizeof(double2), &pR)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 5, (long long)K * (nb + 1) * sizeof(int), &pPiv)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pRed)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 7, (2 * bn + r2) * K * sizeof(double2), &pW)) != RSFD_OK) return s;
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = handle_stream(h);
+  double2* dG0 = (double2*)pG0;
+  double2* dM = (double2*)pM;
+  double2* dLU = (double2*)pLU;
+  double2* dY = (double2*)pY;
+  double2* dR = (double2*)pR;
+  double2* dRHS = (double2*)pW;
+  double2* dW = dRHS + bn * K;
+  double2* dX = dW + bn * K;
+  int* piv = (int*)pPiv;
+  int* info = piv + (long long)K * nb;
+  double* red = (double*)pRed;
+  const long long rtot = r2 * K, btot = b2 * K, ntot = bn * K;
+  if (fp64) copy_c128<<<grid_for(rtot), 256, 0, st>>>((const double2*)G0, dG0, rtot);
+  else to_c128<float2><<<grid_for(rtot), 256, 0, st>>>((const float2*)G0, dG0, rtot);
+  const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  // M = I - G0_bb Sigma (G0_bb: the leading nb x nb block of G0, leading dimension nr)
+  set_identity<<<grid_for(btot), 256, 0, st>>>(dM, nb, K);
+  zgemm(st, K, nb, ns, ns, m1, dG0, nr, r2, 0, (const double2*)SL, ns, (long long)ns * ns, one, dM, nb, b2);
+  zgemm(st, K, nb, ns, ns, m1, dG0 + (long long)ns * nr, nr, r2, 0, (const double2*)SR, ns, (long long)ns * ns, one,
+        dM + (long long)ns * nb, nb, b2);
+  copy_c128<<<grid_for(btot), 256, 0, st>>>(dM, dLU, btot);
+  DY_CK(h, cudaMemsetAsync(info, 0, K * sizeof(int), st));
+  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  // Y = M^{-1} G0[b, :] with two FP64 refinement steps
+  copy_rows_c128<<<grid_for(ntot), 256, 0, st>>>(dG0, nr, dRHS, nb, nb, nr, K);
+  copy_c128<<<grid_for(ntot), 256, 0, st>>>(dRHS, dY, ntot);
+  dim3 g((nr + 127) / 128, K);
+  zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dY, nb, nr);
+  for (int it = 0; it < 2; ++it) {
+    copy_c128<<<grid_for(ntot), 256, 0, st>>>(dRHS, dR, ntot);
+    zgemm(st, K, nb, nr, nb, m1, dM, nb, b2, 0, dY, nb, bn, one, dR, nb, bn);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dR, nb, nr);
+    axpy_c128<<<grid_for(ntot), 256, 0, st>>>(dY, dR, ntot);
+  }
+  if (refres) {
+    copy_c128<<<grid_for(ntot), 256, 0, st>>>(dRHS, dR, ntot);
+    zgemm(st, K, nb, nr, nb, m1, dM, nb, b2, 0, dY, nb, bn, one, dR, nb, bn);
+    frob2_batched<<<K, 256, 0, st>>>(dR, bn, red);
+    frob2_batched<<<K, 256, 0, st>>>(dRHS, bn, red + K);
+  }
+  // W = Sigma Y (block-diagonal Sigma), then G = G0 + G0[:, b] W
+  zgemm(st, K, ns, nr, ns, one, (const double2*)SL, ns, (long long)ns * ns, 0, dY, nb, bn, zero, dW, nb, bn);
+  zgemm(st, K, ns, nr, ns, one, (const double2*)SR, ns, (long long)ns * ns, 0, dY + ns, nb, bn, zero, dW + ns, nb, bn);
+  copy_c128<<<grid_for(rtot), 256, 0, st>>>(dG0, dX, rtot);
+  zgemm(st, K, nr, nr, nb, one, dG0, nr, r2, 0, dW, nb, bn, one, dX, nr, r2);
+  if (fp64) copy_c128<<<grid_for(rtot), 256, 0, st>>>(dX, (double2*)G, rtot);
+  else from_c128_f<<<grid_for(rtot), 256, 0, st>>>(dX, (float2*)G, rtot);
+  DY_CK(h, cudaGetLastError());
+  std::vector<int> hinfo(K);
+  DY_CK(h, cudaMemcpyAsync(hinfo.data(), info, K * sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hred(2 * K);
+  if (refres) DY_CK(h, cudaMemcpyAsync(hred.data(), red, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DY_CK(h, cudaStreamSynchronize(st));
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  if (refres)
+    for (int k = 0; k < K; ++k) refres[k] = sqrt(hred[k]) / sqrt(hred[K + k] > 0 ? hred[K + k] : 1.0);
+  for (int k = 0; k < K; ++k)
+    if (hinfo[k] != 0)
+      return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_dyson_tracked: singular I - G0 Sigma at energy " + std::to_string(k));
   return RSFD_OK;
 }
 

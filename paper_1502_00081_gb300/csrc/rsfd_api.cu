@@ -40,6 +40,8 @@ struct Handle {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int device = 0;
   std::vector<int64_t> brow;
+  std::vector<int> track;      // tracked interior planes (rows recorded after b)
+  int nr = 0;                  // recorded rows: nb + track.size() * Nx * Ny
   void* dV = nullptr;
   int64_t* dbrow = nullptr;
   // nonlocal projectors (host copy; the device path for them is not built yet)
@@ -292,6 +294,7 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   memset(&h->stats, 0, sizeof(h->stats));
   const long long nxy = (long long)h->nx * h->ny;
   h->nb = (int)(2 * n_face * nxy);
+  h->nr = h->nb;
   h->brow.resize(h->nb);
   for (int pl = 0; pl < 2 * n_face; ++pl) {
     const long long z = pl < n_face ? pl : (h->nz - 2 * n_face + pl);
@@ -347,6 +350,37 @@ rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows) {
   if (!h || !nb) return fail(h, RSFD_ERR_ARG, "rsfd_boundary_rows: NULL argument");
   *nb = h->nb;
   if (rows) memcpy(rows, h->brow.data(), h->nb * sizeof(int64_t));
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_set_tracked_planes(rsfd_handle h, int32_t n, const int32_t* z) {
+  if (!h) return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: NULL handle");
+  if (n < 0 || n > RSFD_MAX_TRACKED_PLANES || (n > 0 && !z))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: need 0 <= n <= " + std::to_string(RSFD_MAX_TRACKED_PLANES));
+  std::vector<int> t(z, z + n);
+  for (int i = 0; i < n; ++i) {
+    if (t[i] < h->nface || t[i] >= h->nz - h->nface)
+      return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: plane " + std::to_string(t[i]) + " is not an interior plane");
+    for (int j = 0; j < i; ++j)
+      if (t[j] == t[i]) return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: repeated plane");
+  }
+  const long long nxy = (long long)h->nx * h->ny;
+  const long long nr = h->nb + (long long)n * nxy;
+  if (nr > (1ll << 30)) return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: too many recorded rows");
+  h->track = t;
+  h->nr = (int)nr;
+  return RSFD_OK;
+}
+
+rsfd_status rsfd_tracked_rows(rsfd_handle h, int32_t* nr, int64_t* rows) {
+  if (!h || !nr) return fail(h, RSFD_ERR_ARG, "rsfd_tracked_rows: NULL argument");
+  *nr = h->nr;
+  if (rows) {
+    memcpy(rows, h->brow.data(), h->nb * sizeof(int64_t));
+    const long long nxy = (long long)h->nx * h->ny;
+    for (size_t e = 0; e < h->track.size(); ++e)
+      for (long long o = 0; o < nxy; ++o) rows[h->nb + e * nxy + o] = (long long)h->track[e] * nxy + o;
+  }
   return RSFD_OK;
 }
 
@@ -420,7 +454,9 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.N = h->N;
   d.R = h->R;
   d.nface = h->nface;
-  d.nb = h->nb;
+  d.nb = h->nr;
+  d.ntrack = (int)h->track.size();
+  for (int e = 0; e < d.ntrack; ++e) d.track[e] = h->track[e];
   d.K = K;
   d.ncols = ncols;
   d.kind = resolve_kind(prec, h->opts.pass_kind);
@@ -466,7 +502,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   {
     size_t freeb = 0, totb = 0;
     RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));
-    const size_t per_slot = (size_t)d.nvec * vec * vsz + 2 * (size_t)K * h->nb * vsz + (size_t)C * h->nb * hsz +
+    const size_t per_slot = (size_t)d.nvec * vec * vsz + 2 * (size_t)K * h->nr * vsz + (size_t)C * h->nr * hsz +
                             (size_t)K * C * sizeof(ShiftCoef) + (size_t)K * sizeof(ShiftState) +
                             (size_t)d.ctas_per_slot * 64 + 256;
     const size_t have = h->rbuf.bytes + h->xbuf.bytes + h->pbuf.bytes + h->rhist.bytes + h->coef.bytes;
@@ -481,9 +517,9 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   // ---- workspace
   rsfd_status s;
   if ((s = ensure(h, h->rbuf, (size_t)W * d.nvec * vec * vsz)) != RSFD_OK) return s;
-  if ((s = ensure(h, h->xbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
-  if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nb * vsz)) != RSFD_OK) return s;
-  if ((s = ensure(h, h->rhist, (size_t)W * C * h->nb * hsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->xbuf, (size_t)W * K * h->nr * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nr * vsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->rhist, (size_t)W * C * h->nr * hsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->coef, (size_t)W * K * C * sizeof(ShiftCoef))) != RSFD_OK) return s;
   if ((s = ensure(h, h->eflag, 16)) != RSFD_OK) return s;
   if ((s = ensure(h, h->slots, (size_t)W * sizeof(SlotState))) != RSFD_OK) return s;
@@ -709,6 +745,14 @@ rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Si
   if (!G0_bb || !Sigma_L || !Sigma_R || !G_bb || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_boundary: bad arguments");
   if (G0_bb == G_bb) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_boundary: G_bb may not alias G0_bb");
   return dyson_run(h, G0_bb, Sigma_L, Sigma_R, K, G_bb, refine_residual);
+}
+
+rsfd_status rsfd_dyson_tracked(rsfd_handle h, const void* G0, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                               void* G, double* refine_residual) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_tracked: NULL handle");
+  if (!G0 || !Sigma_L || !Sigma_R || !G || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_tracked: bad arguments");
+  if (G0 == G) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_tracked: G may not alias G0");
+  return dyson_tracked_run(h, h->nr, G0, Sigma_L, Sigma_R, K, G, refine_residual);
 }
 
 rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,

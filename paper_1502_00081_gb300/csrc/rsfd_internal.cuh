@@ -98,13 +98,15 @@ struct SolveDims {
   long long N;
   int R;              // stencil reach (fd_order / 2)
   int nface;          // boundary planes per side
-  int nb;             // boundary rows
+  int nb;             // recorded rows per column: the boundary rows, then the tracked planes
   int K;              // energies
   int W;              // slots
   int tile_y;         // stencil tile height (y); the tile width in x is fixed by the kernel
   int depth;          // TMA prefetch depth of the pass kernel
   int tiles_x, tiles_y, zchunk, nzchunks, ctas_per_slot;
   int ncols;
+  int ntrack;         // interior planes recorded after the boundary planes
+  int track[16];      // their z indices (rows 2 nface Nx Ny + e Nx Ny ...)
   int kind;           // RSFD_PASS_RECOMPUTE or RSFD_PASS_STORED
   int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
   int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
@@ -184,6 +186,8 @@ rsfd_status handle_end(Handle* h);
 
 // Dyson / transmission launchers (dyson.cu).
 rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres);
+rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL, const void* SR, int K, void* G,
+                              double* refres);
 rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const void* SR, int K, double* T);
 
 // Host lead self-energy (lead_sigma.cpp).

@@ -124,3 +124,47 @@ def test_mixed_handle_dyson_T(rs, prec):
         Gd = g_dense(p, Z, SLo, SRo, rows=b, cols=b)
         assert np.linalg.norm(Gg[k] - Gd) / np.linalg.norm(Gd) <= 1e-5
         assert abs(T[k] - transmission(Gd, SLo, SRo)[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,bound", [("FP64", 1e-9), ("DF64", 1e-6)])
+def test_tracked_planes_interior_blocks(rs, prec, bound):
+    """Interior diagonal blocks G_T(z_l, z_l) (Sec. III B, after Eq. sec3-06): the solver records two
+    interior planes next to b, the Dyson step on the recorded rows gives the perturbed blocks, and
+    both match the oracle: the shifted-COCG G0 on those rows and columns, and the dense
+    (Z - H - Sigma)^{-1}.  The boundary block equals rsfd_dyson_boundary's, and the plane's density of
+    states -Im Tr G(l,l) / pi is positive."""
+    p = make_problem("tiny_wire_fp64")
+    planes = [4, 7]
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=getattr(rs, "RSFD_" + prec)) as h:
+        rs.rsfd_set_tracked_planes(h.ptr, planes)
+        trows = rs.rsfd_tracked_rows(h.ptr)
+        nb, nr = h.nb, trows.size
+        assert nr == nb + len(planes) * p.grid[0] * p.grid[1]
+        assert np.array_equal(trows[:nb], h.rows)
+        G0 = torch.zeros((p.K, nr, nr), dtype=torch.complex128, device="cuda")
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, trows, p.energies, p.eta, p.tol, p.maxit, G0)
+        assert st == rs.RSFD_OK
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+        SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
+        G = torch.empty_like(G0)
+        ref = rs.rsfd_dyson_tracked(h.ptr, G0, SL, SR, G)
+        Gbb = torch.empty((p.K, nb, nb), dtype=torch.complex128, device="cuda")
+        rs.rsfd_dyson_boundary(h.ptr, G0[:, :nb, :nb].contiguous(), SL, SR, Gbb)
+        G0m, Gm, Gbbm = _mat(G0), _mat(G), _mat(Gbb)
+        rs.rsfd_set_tracked_planes(h.ptr, [])
+        assert rs.rsfd_tracked_rows(h.ptr).size == nb
+    assert (ref < 1e-12).all()
+    G0o, _ = shifted_cocg_columns(p, cols=trows, rows=trows, tol=1e-13)
+    assert np.linalg.norm(G0m - G0o) / np.linalg.norm(G0o) <= bound
+    nxy = p.grid[0] * p.grid[1]
+    for k, E in enumerate(p.energies):
+        Z = E + 1j * p.eta
+        SLo, SRo = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
+        Gd = g_dense(p, Z, SLo, SRo, rows=trows, cols=trows)
+        assert np.linalg.norm(Gm[k] - Gd) / np.linalg.norm(Gd) <= bound
+        assert np.linalg.norm(Gm[k][:nb, :nb] - Gbbm[k]) <= 1e-12 * np.linalg.norm(Gbbm[k])
+        for e in range(len(planes)):
+            blk = slice(nb + e * nxy, nb + (e + 1) * nxy)
+            dos = -np.trace(Gm[k][blk, blk]).imag / np.pi
+            dos_o = -np.trace(Gd[blk, blk]).imag / np.pi
+            assert dos > 0 and abs(dos - dos_o) <= 10 * bound * abs(dos_o)
