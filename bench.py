@@ -19,9 +19,15 @@ no collective on the data path); the step time is the maximum over ranks.
 
 from __future__ import annotations
 
+import os
+
+# the CPU oracle leg is timed single-threaded (the "cores" it reports); pin the host BLAS pools before
+# numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -374,7 +380,11 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": p.name, "grid": list(p.grid), "energies": p.K, "columns_per_gpu": int(p.cols.size)},
+           "config": {"workload": p.name, "grid": list(p.grid), "h": p.h, "fd_order": p.fd_order,
+                      "columns_per_step": min(args.cols_per_step, int(p.cols.size)) if args.cols_per_step > 0
+                      else int(p.cols.size), "columns_in_sample": int(p.cols.size),
+                      "energies": p.K, "eta": p.eta, "tol": p.tol,
+                      "sample": "each step times a bounded number of seed iterations of one column"},
            "impl": "reference",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descr["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -5,7 +5,8 @@
 // (equivalent to the block formulas Eqs. sec3-02 ... sec3-06).  Every energy is an independent
 // dense complex solve of size nb; the batch is processed with:
 //   1. M = I - G0 Sigma           (batched complex GEMM, FP64)
-//   2. M = P L U                  (batched right-looking LU with partial pivoting, FP64)
+//   2. M = P L U                  (batched blocked right-looking LU with partial pivoting, FP64;
+//                                  panels of 32 columns, trailing updates by the batched GEMM)
 //   3. G = U^{-1} L^{-1} P G0     (batched triangular solves)
 //   4. FP64 iterative refinement: R = G0 - M G, G += M^{-1} R (twice), reporting ||R||/||G0||.
 // T(E) = Tr[Gamma_L G_RL^H Gamma_R G_RL] (Eq. TF) with Gamma = i (Sigma - Sigma^H) is two
@@ -104,8 +105,13 @@ __global__ void set_identity(double2* M, int nb, int batch) {
   }
 }
 
-// In-place LU with partial pivoting of one nb x nb matrix per CTA (right-looking, unblocked).
-__global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* piv, int* info) {
+// Blocked right-looking LU with partial pivoting (LAPACK getrf order: piv[j] is the row exchanged
+// with row j at step j).  Panels of kPanel columns are factorised by one CTA per matrix; the row
+// exchanges are then applied to the other columns, U12 = L11^{-1} A12 is solved, and the trailing
+// block is updated by the batched GEMM, which spreads the O(nb^3) work over every SM.
+constexpr int kPanel = 32;
+
+__global__ void __launch_bounds__(256) panel_getrf(double2* M, int nb, int j0, int jb, int* piv, int* info) {
   const int b = blockIdx.x;
   double2* A = M + (long long)b * nb * nb;
   int* pv = piv + (long long)b * nb;
@@ -113,8 +119,7 @@ __global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* p
   __shared__ int s_idx[256];
   __shared__ int s_p;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int j = 0; j < nb; ++j) {
-    // pivot search in column j
+  for (int j = j0; j < j0 + jb; ++j) {
     double best = -1.0;
     int bi = j;
     for (int i = j + tid; i < nb; i += nt) {
@@ -124,11 +129,11 @@ __global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* p
     s_val[tid] = best;
     s_idx[tid] = bi;
     __syncthreads();
-    for (int s = nt / 2; s > 0; s >>= 1) {
-      if (tid < s) {
-        if (s_val[tid + s] > s_val[tid] || (s_val[tid + s] == s_val[tid] && s_idx[tid + s] < s_idx[tid])) {
-          s_val[tid] = s_val[tid + s];
-          s_idx[tid] = s_idx[tid + s];
+    for (int s2 = nt / 2; s2 > 0; s2 >>= 1) {
+      if (tid < s2) {
+        if (s_val[tid + s2] > s_val[tid] || (s_val[tid + s2] == s_val[tid] && s_idx[tid + s2] < s_idx[tid])) {
+          s_val[tid] = s_val[tid + s2];
+          s_idx[tid] = s_idx[tid + s2];
         }
       }
       __syncthreads();
@@ -136,12 +141,12 @@ __global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* p
     if (tid == 0) {
       s_p = s_idx[0];
       pv[j] = s_p;
-      if (!(s_val[0] > 0.0)) info[b] = j + 1;
+      if (!(s_val[0] > 0.0) && info[b] == 0) info[b] = j + 1;
     }
     __syncthreads();
     const int p = s_p;
-    if (p != j) {
-      for (int c = tid; c < nb; c += nt) {
+    if (p != j) {   // exchange rows j and p inside the panel
+      for (int c = j0 + tid; c < j0 + jb; c += nt) {
         const double2 t = A[(long long)c * nb + j];
         A[(long long)c * nb + j] = A[(long long)c * nb + p];
         A[(long long)c * nb + p] = t;
@@ -152,15 +157,53 @@ __global__ void __launch_bounds__(256) zgetrf_batched(double2* M, int nb, int* p
     const double2 inv = (d.x != 0.0 || d.y != 0.0) ? cdiv(make_double2(1.0, 0.0), d) : make_double2(0.0, 0.0);
     for (int i = j + 1 + tid; i < nb; i += nt) A[(long long)j * nb + i] = cmul(A[(long long)j * nb + i], inv);
     __syncthreads();
-    const int rem = nb - j - 1;
-    const long long tot = (long long)rem * rem;
+    const int rem_r = nb - j - 1, rem_c = j0 + jb - j - 1;
+    const long long tot = (long long)rem_r * rem_c;
     for (long long t = tid; t < tot; t += nt) {
-      const int c = j + 1 + (int)(t / rem), i = j + 1 + (int)(t % rem);
+      const int c = j + 1 + (int)(t / rem_r), i = j + 1 + (int)(t % rem_r);
       const double2 l = A[(long long)j * nb + i], u = A[(long long)c * nb + j];
       double2& a = A[(long long)c * nb + i];
       a = csub(a, cmul(l, u));
     }
     __syncthreads();
+  }
+}
+
+// apply the exchanges of rows j0 .. j0 + jb - 1 (in order) to every column outside the panel
+__global__ void panel_laswp(double2* M, int nb, int j0, int jb, const int* piv, int batch) {
+  const int ncol = nb - jb;
+  const long long tot = (long long)ncol * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ncol);
+    int c = (int)(t - (long long)b * ncol);
+    if (c >= j0) c += jb;
+    double2* col = M + (long long)b * nb * nb + (long long)c * nb;
+    const int* pv = piv + (long long)b * nb;
+    for (int j = j0; j < j0 + jb; ++j) {
+      const int p = pv[j];
+      if (p != j) {
+        const double2 x = col[j];
+        col[j] = col[p];
+        col[p] = x;
+      }
+    }
+  }
+}
+
+// U12 = L11^{-1} A12 (L11 unit lower jb x jb), one thread per column right of the panel
+__global__ void panel_trsm(double2* M, int nb, int j0, int jb, int batch) {
+  const int ncol = nb - j0 - jb;
+  const long long tot = (long long)ncol * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / ncol);
+    const int c = j0 + jb + (int)(t - (long long)b * ncol);
+    double2* A = M + (long long)b * nb * nb;
+    double2* col = A + (long long)c * nb;
+    for (int i = j0 + 1; i < j0 + jb; ++i) {
+      double2 s = col[i];
+      for (int k = j0; k < i; ++k) s = csub(s, cmul(A[(long long)k * nb + i], col[k]));
+      col[i] = s;
+    }
   }
 }
 
@@ -273,6 +316,24 @@ int grid_for(long long n) {
   return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
 }
 
+// batched blocked LU of K matrices nb x nb (column-major, contiguous), in place
+void getrf_blocked(cudaStream_t st, double2* M, int nb, int K, int* piv, int* info) {
+  const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  const long long n2 = (long long)nb * nb;
+  for (int j0 = 0; j0 < nb; j0 += kPanel) {
+    const int jb = nb - j0 < kPanel ? nb - j0 : kPanel;
+    panel_getrf<<<K, 256, 0, st>>>(M, nb, j0, jb, piv, info);
+    if (nb > jb) panel_laswp<<<grid_for((long long)(nb - jb) * K), 256, 0, st>>>(M, nb, j0, jb, piv, K);
+    const int rest = nb - j0 - jb;
+    if (rest > 0) {
+      panel_trsm<<<grid_for((long long)rest * K), 256, 0, st>>>(M, nb, j0, jb, K);
+      // A22 -= L21 U12
+      zgemm(st, K, rest, rest, jb, m1, M + (long long)j0 * nb + j0 + jb, nb, n2, 0, M + (long long)(j0 + jb) * nb + j0,
+            nb, n2, one, M + (long long)(j0 + jb) * nb + j0 + jb, nb, n2);
+    }
+  }
+}
+
 }  // namespace
 
 #define DY_CK(h, call)                                                                                  \
@@ -316,7 +377,7 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
         dM + (long long)ns * nb, nb, n2);
   copy_c128<<<grid_for(tot), 256, 0, st>>>(dM, dLU, tot);
   DY_CK(h, cudaMemsetAsync(info, 0, K * sizeof(int), st));
-  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  getrf_blocked(st, dLU, nb, K, piv, info);
   copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dX, tot);
   {
     dim3 g((nb + 127) / 128, K);
@@ -396,7 +457,7 @@ rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL,
         dM + (long long)ns * nb, nb, b2);
   copy_c128<<<grid_for(btot), 256, 0, st>>>(dM, dLU, btot);
   DY_CK(h, cudaMemsetAsync(info, 0, K * sizeof(int), st));
-  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  getrf_blocked(st, dLU, nb, K, piv, info);
   // Y = M^{-1} G0[b, :] with two FP64 refinement steps
   copy_rows_c128<<<grid_for(ntot), 256, 0, st>>>(dG0, nr, dRHS, nb, nb, nr, K);
   copy_c128<<<grid_for(ntot), 256, 0, st>>>(dRHS, dY, ntot);
@@ -565,7 +626,7 @@ extern "C" rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const 
   zgemm(st, K, nb, ns, ns, m1, G0 + (long long)ns * nb, nb, n2, 0, (const double2*)Sigma_R, ns, (long long)ns * ns, one,
         dM + (long long)ns * nb, nb, n2);
   copy_c128<<<grid_for(tot), 256, 0, st>>>(dM, dLU, tot);
-  zgetrf_batched<<<K, 256, 0, st>>>(dLU, nb, piv, info);
+  getrf_blocked(st, dLU, nb, K, piv, info);
   copy_c128<<<grid_for(tot), 256, 0, st>>>(G0, dX, tot);
   dim3 g((nb + 127) / 128, K);
   zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dX, nb, nb);

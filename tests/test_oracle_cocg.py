@@ -8,8 +8,10 @@
 * The true residual b - (Z_i - H) x^(i) matches the collinear estimate
   ||r_n|| / |pi_n^(i)| (Eq. collinear).
 * G0 is complex symmetric (G^T = G).
-* Planted mistakes (a conjugated bilinear form, a flipped shift sign, a
-  dropped r_{n-2} term) make the comparison with the dense solve fail.
+* Planted mistakes make the comparison with the dense solve fail: a conjugated
+  bilinear form, a flipped shift sign, and (in a copy of the oracle's source) a
+  dropped r_{n-2} term of Eq. rvec, a dropped pi_{n-1} term of Eq. spi and an
+  unsquared pi ratio in Eq. sbeta.
 """
 
 import numpy as np
@@ -112,12 +114,13 @@ def test_columns_and_rows_restriction():
         assert np.abs(G[k] - G[k].T).max() < 1e-9 * np.abs(G[k]).max()
 
 
-def _shifted_err(p, patched):
+def _shifted_err(p, patched, mod=None):
+    mod = oc if mod is None else mod
     H, P, wE = hamiltonian(p)
     Z = p.energies + 1j * p.eta
     b = np.zeros(p.N, complex)
     b[5] = 1
-    r = oc.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-10, maxit=2000)
+    r = mod.shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, 1e-10, maxit=2000)
     errs = []
     for k in range(Z.size):
         xd = g0_dense(p, Z[k], cols=[5])[:, 0]
@@ -159,3 +162,34 @@ def test_chain_shifted_dyson_transmission_matches_dense():
         Gd = g_dense(p, Z, SL, SR, rows=b, cols=b)
         assert np.linalg.norm(G - Gd) / np.linalg.norm(Gd) < 1e-9
         assert abs(transmission(G, SL, SR)[0] - transmission(Gd, SL, SR)[0]) < 1e-9
+
+
+def _planted_module(old, new):
+    """A copy of oracle/cocg.py with one source line changed (the committed oracle is untouched)."""
+    import inspect
+    import sys
+    import types
+    src = inspect.getsource(oc)
+    assert old in src
+    mod = types.ModuleType("oracle_cocg_planted")
+    sys.modules[mod.__name__] = mod          # dataclasses resolve their module by name
+    try:
+        exec(compile(src.replace(old, new), "oracle_cocg_planted", "exec"), mod.__dict__)
+    finally:
+        del sys.modules[mod.__name__]
+    return mod
+
+
+@pytest.mark.parametrize("old,new", [
+    # the r_{n-2} term of the three-term residual recurrence (Eq. rvec)
+    ("r_np1 = (1.0 + c_n) * r_n - alpha_n * Ar - c_n * r_nm1", "r_np1 = (1.0 + c_n) * r_n - alpha_n * Ar"),
+    # the pi_{n-1} term of the shifted recurrence (Eq. spi)
+    ("pi_np1 = (1.0 + c_n + alpha_n * sigma[a]) * pi_n[a] - c_n * pi_nm1[a]",
+     "pi_np1 = (1.0 + c_n + alpha_n * sigma[a]) * pi_n[a]"),
+    # the square of the pi ratio in the shifted beta (Eq. sbeta)
+    ("beta_i = (pi_nm1[a] / pi_n[a]) ** 2 * beta_nm1", "beta_i = (pi_nm1[a] / pi_n[a]) * beta_nm1"),
+])
+def test_planted_recurrence_mistakes_are_caught(old, new):
+    p = small_problem(grid=(4, 4, 6), h=0.5, fd_order=2, n_wells=2, n_energies=4, eta=3e-2)
+    assert _shifted_err(p, None) < 1e-8
+    assert _shifted_err(p, "planted", _planted_module(old, new)) > 1e-4
