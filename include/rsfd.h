@@ -109,6 +109,14 @@ typedef enum {
                               one stencil application per grid point */
 } rsfd_pass_kind;
 
+/* Form of the Dyson solve (rsfd_solve_opts.dyson_kind). */
+typedef enum {
+  RSFD_DYSON_AUTO = 0, /* RSFD_DYSON_TC for double-float and complex64 handles, RSFD_DYSON_FP64 for FP64 handles */
+  RSFD_DYSON_FP64 = 1, /* LU, triangular solves and refinement in FP64 on the CUDA cores */
+  RSFD_DYSON_TC = 2    /* LU and triangular solves in FP32 with their O(nb^3) updates on the tensor cores
+                          (3xTF32, rsfd_cgemm_tf32x3), FP64 residuals and corrections (iterative refinement) */
+} rsfd_dyson_kind;
+
 /* Launch options of the solver; zero fields mean "choose automatically". */
 typedef struct {
   int32_t slots;          /* columns iterated together (RHS block width) */
@@ -123,6 +131,8 @@ typedef struct {
   int32_t pass_kind;      /* rsfd_pass_kind */
   int32_t prefetch;       /* z-planes of input the pass keeps in flight (TMA), 1..7 */
   int32_t rows_per_thread;/* RSFD_PASS_STORED: tile rows per thread, 1, 2 or 4 (tile_y must be a multiple) */
+  int32_t dyson_kind;     /* rsfd_dyson_kind of rsfd_dyson_boundary */
+  int32_t dyson_refine;   /* FP64 refinement steps of rsfd_dyson_boundary (0 = 2; at most 8) */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */
@@ -201,13 +211,30 @@ rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out);
  *   (I - G0_bb(k) Sigma_bb(k)) G_bb(k) = G0_bb(k),  Sigma_bb = diag(Sigma_L, Sigma_R),
  * for every k < K.  G0_bb must hold all boundary columns in b order
  * (ncols = nb).  The solve is an LU with partial pivoting followed by FP64
- * iterative refinement of the residual G0 - (I - G0 Sigma) G.
+ * iterative refinement of the residual G0 - (I - G0 Sigma) G.  Form (rsfd_solve_opts.dyson_kind):
+ * FP64 LU on the CUDA cores (FP64 handles by default), or FP32 LU and triangular solves whose
+ * updates run on the tensor cores (3xTF32) with FP64 residuals (double-float and complex64 handles
+ * by default); energies are processed in chunks that fit the free device memory.
  *   G0_bb    device [K][nb][nb] (handle precision).
  *   Sigma_L, Sigma_R  device [K][ns][ns] c128.
  *   G_bb     device output, same layout and type as G0_bb (may not alias G0_bb).
  *   refine_residual  host [K] (nullable): ||G0 - M G||_F / ||G0||_F after refinement. */
 rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
                                 int32_t K, void* G_bb, double* refine_residual);
+
+/* Batched complex GEMM on the tensor cores: the building block of the Dyson solve's LU and triangular
+ * solves (Eq. sec3-01a; see rsfd_dyson_boundary), exposed for direct use and testing.
+ *   C[b] = alpha A[b] B[b] + beta C[b],  b < batch,
+ * complex FP32 (interleaved re, im floats), column-major.  Every product is taken in 3xTF32 form
+ * (hi*hi + hi*lo + lo*hi of the TF32 splits) with FP32 accumulation: FP32-class accuracy.
+ *   A  device m x k, leading dimension lda >= m, batch stride sA (complex elements);
+ *   B  device k x n, ldb >= k, stride sB;  C device m x n, ldc >= m, stride sC (may not overlap A, B);
+ *   alpha host [2] (re, im);  beta 0 or 1;  stream cudaStream_t (NULL = legacy default stream).
+ * The call synchronises the stream.  RSFD_ERR_ARG for bad sizes or beta, RSFD_ERR_CUDA for a launch
+ * failure, RSFD_ERR_TIMEOUT when the kernel's bounded wait on its tensor-core operations expired. */
+rsfd_status rsfd_cgemm_tf32x3(int32_t batch, int32_t m, int32_t n, int32_t k, const double* alpha, const void* A,
+                              int32_t lda, int64_t sA, const void* B, int32_t ldb, int64_t sB, double beta, void* C,
+                              int32_t ldc, int64_t sC, void* stream);
 
 /* Dyson step on the recorded row set (Eq. sec3-01a with Sigma supported on b; the interior blocks
  * G_T(z_0, z_l), G_T(z_l, z_l) of Sec. III B):

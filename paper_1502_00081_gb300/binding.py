@@ -30,6 +30,9 @@ RSFD_SEED_INDEX = 2
 RSFD_PASS_AUTO = 0
 RSFD_PASS_RECOMPUTE = 1
 RSFD_PASS_STORED = 2
+RSFD_DYSON_AUTO = 0
+RSFD_DYSON_FP64 = 1
+RSFD_DYSON_TC = 2
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_ALLOC", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED", 5: "ERR_BREAKDOWN",
            6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
@@ -55,7 +58,8 @@ class rsfd_col_info(ctypes.Structure):
 class rsfd_solve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32)]
+                ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
+                ("dyson_kind", ctypes.c_int32), ("dyson_refine", ctypes.c_int32)]
 
 
 class rsfd_stats(ctypes.Structure):
@@ -83,6 +87,10 @@ _SIGNATURES = {
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
     "rsfd_dyson_boundary": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_dyson_tracked": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_cgemm_tf32x3": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_double), _P, ctypes.c_int32, ctypes.c_int64, _P,
+                                         ctypes.c_int32, ctypes.c_int64, ctypes.c_double, _P, ctypes.c_int32,
+                                         ctypes.c_int64, _P]),
     "rsfd_transmission": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_lead_sigma_uniform": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_int32,
@@ -218,10 +226,10 @@ def rsfd_boundary_rows(h):
 
 
 def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0,
-                           pass_kind=0, prefetch=0, rows_per_thread=0):
+                           pass_kind=0, prefetch=0, rows_per_thread=0, dyson_kind=0, dyson_refine=0):
     lib = load_library()
     o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile),
-                        int(pass_kind), int(prefetch), int(rows_per_thread))
+                        int(pass_kind), int(prefetch), int(rows_per_thread), int(dyson_kind), int(dyson_refine))
     _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
 
 
@@ -262,6 +270,27 @@ def rsfd_dyson_boundary(h, G0_bb, Sigma_L, Sigma_R, G_bb):
     ref = np.zeros(K, np.float64)
     _check(h, lib.rsfd_dyson_boundary(h, p0, pl, pr, K, pg, ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return ref
+
+
+def rsfd_cgemm_tf32x3(A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C[b] = alpha A[b] B[b] + beta C[b] on the tensor cores (3xTF32).  A, B, C: complex64 CUDA tensors of
+    shape [batch, cols, rows] holding column-major matrices (rows fastest); C is written in place."""
+    import torch
+    lib = load_library()
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        if t.dtype != torch.complex64 or not t.is_cuda or t.dim() != 3 or not t.is_contiguous():
+            raise RsfdError(RSFD_ERR_ARG, f"{nm}: contiguous complex64 CUDA tensor [batch, cols, rows] expected")
+    batch, k, m = A.shape
+    n = B.shape[1]
+    if B.shape[0] != batch or B.shape[2] != k or tuple(C.shape) != (batch, n, m):
+        raise RsfdError(RSFD_ERR_ARG, "shape mismatch")
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.rsfd_cgemm_tf32x3(int(batch), int(m), int(n), int(k), al, A.data_ptr(), int(m), int(m * k),
+                               B.data_ptr(), int(k), int(k * n), float(beta), C.data_ptr(), int(m), int(m * n),
+                               ctypes.c_void_p(stream))
+    _check(None, st)
 
 
 def rsfd_dyson_boundary_noalloc(G0_bb, Sigma_L, Sigma_R, G_bb, stream=None):

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librsfd.so")
 
-SOURCES = ["rsfd_api.cu", "cocg_kernels.cu", "dyson.cu", "lead_sigma.cpp"]
+SOURCES = ["rsfd_api.cu", "cocg_kernels.cu", "dyson.cu", "tc_gemm.cu", "lead_sigma.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -342,7 +342,117 @@ void getrf_blocked(cudaStream_t st, double2* M, int nb, int K, int* piv, int* in
     if (e_ != cudaSuccess) return handle_fail((h), RSFD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+__global__ void to_f32_c(const double2* src, float2* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+__global__ void add_f32_to_c128(double2* y, const float2* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = make_double2(y[i].x + (double)x[i].x, y[i].y + (double)x[i].y);
+}
+__global__ void set_f32_to_c128(double2* y, const float2* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = make_double2((double)x[i].x, (double)x[i].y);
+}
+
+// Tensor-core form of the Dyson step, energies processed in chunks that fit the device:
+//   M = I - G0 Sigma                       FP64 (CUDA cores)
+//   F = P L U of M in FP32                 panels on the CUDA cores, trailing updates 3xTF32 (tcgen05)
+//   X = F^{-1} G0                          blocked triangular solves, updates 3xTF32 (tcgen05)
+//   nref times: R = G0 - M X (FP64), X += F^{-1} R
+// Reported residual ||G0 - M X|| / ||G0|| is the FP64 one after the last correction.
+rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres) {
+  const int nb = handle_nb(h);
+  const int ns = nb / 2;
+  const long long n2 = (long long)nb * nb, s2 = (long long)ns * ns;
+  const bool fp64in = handle_prec(h) != RSFD_MIXED;
+  const int nref = handle_dyson_refine(h);
+  // per energy: M, X, R (c128), G0 copy when the input is complex64, F and the FP32 solve (c64)
+  const long long per = n2 * (3 * 16 + (fp64in ? 0 : 16) + 2 * 8) + (long long)nb * 8 + 64;
+  size_t free_b = 0, tot_b = 0;
+  DY_CK(h, cudaMemGetInfo(&free_b, &tot_b));
+  long long kc = (long long)(0.6 * (double)free_b) / per;
+  if (kc > K) kc = K;
+  if (kc < 1) kc = 1;
+  const int Kc = (int)kc;
+  rsfd_status s;
+  void *pM, *pX, *pR, *pF, *pXf, *pPiv, *pRed, *pG0;
+  if ((s = handle_ensure(h, 1, n2 * Kc * sizeof(double2), &pM)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 3, n2 * Kc * sizeof(double2), &pX)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, n2 * Kc * sizeof(double2), &pR)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, 2 * n2 * Kc * sizeof(float2), &pF)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 5, ((long long)Kc * (2 * nb + 1) + 1) * sizeof(int), &pPiv)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pRed)) != RSFD_OK) return s;
+  if (!fp64in && (s = handle_ensure(h, 0, n2 * Kc * sizeof(double2), &pG0)) != RSFD_OK) return s;
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = handle_stream(h);
+  double2* dM = (double2*)pM;
+  double2* dX = (double2*)pX;
+  double2* dR = (double2*)pR;
+  float2* dF = (float2*)pF;
+  float2* dXf = dF + n2 * Kc;
+  int* piv = (int*)pPiv;
+  int* perm = piv + (long long)Kc * nb;
+  int* info = perm + (long long)Kc * nb;
+  int* err = info + Kc;
+  double* red = (double*)pRed;
+  const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  DY_CK(h, cudaMemsetAsync(err, 0, sizeof(int), st));
+  std::vector<int> hinfo(K, 0);
+  for (int k0 = 0; k0 < K; k0 += Kc) {
+    const int kb = K - k0 < Kc ? K - k0 : Kc;
+    const long long tot = n2 * kb;
+    const double2* g0;
+    if (fp64in) {
+      g0 = (const double2*)G0 + n2 * k0;
+    } else {
+      to_c128<float2><<<grid_for(tot), 256, 0, st>>>((const float2*)G0 + n2 * k0, (double2*)pG0, tot);
+      g0 = (const double2*)pG0;
+    }
+    const double2* sl = (const double2*)SL + s2 * k0;
+    const double2* sr = (const double2*)SR + s2 * k0;
+    set_identity<<<grid_for(tot), 256, 0, st>>>(dM, nb, kb);
+    zgemm(st, kb, nb, ns, ns, m1, g0, nb, n2, 0, sl, ns, s2, one, dM, nb, n2);
+    zgemm(st, kb, nb, ns, ns, m1, g0 + (long long)ns * nb, nb, n2, 0, sr, ns, s2, one, dM + (long long)ns * nb, nb, n2);
+    to_f32_c<<<grid_for(tot), 256, 0, st>>>(dM, dF, tot);
+    DY_CK(h, cudaMemsetAsync(info, 0, kb * sizeof(int), st));
+    DY_CK(h, getrf_f32_tc(st, dF, nb, kb, piv, info, err));
+    DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, g0, nb, dXf, perm, err));
+    set_f32_to_c128<<<grid_for(tot), 256, 0, st>>>(dX, dXf, tot);
+    for (int it = 0; it < nref; ++it) {
+      copy_c128<<<grid_for(tot), 256, 0, st>>>(g0, dR, tot);
+      zgemm(st, kb, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+      DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, (const double2*)dR, nb, dXf, perm, err));
+      add_f32_to_c128<<<grid_for(tot), 256, 0, st>>>(dX, dXf, tot);
+    }
+    if (refres) {
+      copy_c128<<<grid_for(tot), 256, 0, st>>>(g0, dR, tot);
+      zgemm(st, kb, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
+      frob2_batched<<<kb, 256, 0, st>>>(dR, n2, red + k0);
+      frob2_batched<<<kb, 256, 0, st>>>(g0, n2, red + K + k0);
+    }
+    if (fp64in) copy_c128<<<grid_for(tot), 256, 0, st>>>(dX, (double2*)G + n2 * k0, tot);
+    else from_c128_f<<<grid_for(tot), 256, 0, st>>>(dX, (float2*)G + n2 * k0, tot);
+    DY_CK(h, cudaGetLastError());
+    DY_CK(h, cudaMemcpyAsync(hinfo.data() + k0, info, kb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  int herr = 0;
+  DY_CK(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hred(2 * K);
+  if (refres) DY_CK(h, cudaMemcpyAsync(hred.data(), red, 2 * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DY_CK(h, cudaStreamSynchronize(st));
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  if (herr) return handle_fail(h, RSFD_ERR_TIMEOUT, "rsfd_dyson_boundary: tensor-core GEMM wait expired");
+  if (refres)
+    for (int k = 0; k < K; ++k) refres[k] = sqrt(hred[k]) / sqrt(hred[K + k] > 0 ? hred[K + k] : 1.0);
+  for (int k = 0; k < K; ++k)
+    if (hinfo[k] != 0)
+      return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_dyson_boundary: singular I - G0 Sigma at energy " + std::to_string(k));
+  return RSFD_OK;
+}
+
 rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres) {
+  if (handle_dyson_kind(h) == RSFD_DYSON_TC) return dyson_tc_run(h, G0, SL, SR, K, G, refres);
   const int nb = handle_nb(h);
   const int ns = nb / 2;
   const long long n2 = (long long)nb * nb;

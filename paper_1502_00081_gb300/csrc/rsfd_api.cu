@@ -95,6 +95,11 @@ rsfd_status handle_ensure(Handle* h, int idx, size_t bytes, void** out) {
 cudaStream_t handle_stream(Handle* h) { return h->work; }
 int handle_prec(Handle* h) { return h->prec; }
 int handle_nb(Handle* h) { return h->nb; }
+int handle_dyson_kind(Handle* h) {
+  if (h->opts.dyson_kind != RSFD_DYSON_AUTO) return h->opts.dyson_kind;
+  return h->prec == RSFD_FP64 ? RSFD_DYSON_FP64 : RSFD_DYSON_TC;
+}
+int handle_dyson_refine(Handle* h) { return h->opts.dyson_refine > 0 ? h->opts.dyson_refine : 2; }
 rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& m) { return fail(h, s, m); }
 
 // order the internal stream after the caller's stream
@@ -406,6 +411,10 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
                                    o->tile_y > 0 ? o->tile_y : default_tile_y(h->prec, h->R, h->ny, kind, rows),
                                    o->prefetch, kind) > (size_t)(216 * 1024))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch depth does not fit in shared memory");
+  if (o->dyson_kind < 0 || o->dyson_kind > RSFD_DYSON_TC)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: bad dyson_kind");
+  if (o->dyson_refine < 0 || o->dyson_refine > 8)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: dyson_refine must be 0 .. 8");
   if (o->iters_per_sync > kMaxHist)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: iters_per_sync must be <= " + std::to_string(kMaxHist));
   h->opts = *o;

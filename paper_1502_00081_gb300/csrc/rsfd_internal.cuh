@@ -184,6 +184,21 @@ rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& msg);
 rsfd_status handle_begin(Handle* h);
 rsfd_status handle_end(Handle* h);
 
+int handle_dyson_kind(Handle* h);     // resolved: RSFD_DYSON_FP64 or RSFD_DYSON_TC
+int handle_dyson_refine(Handle* h);   // FP64 refinement steps of the Dyson solve
+
+// Tensor-core building blocks of the Dyson step (tc_gemm.cu).  err: device flag set when a bounded
+// wait of the GEMM kernel expires.
+cudaError_t cgemm_tf32x3(cudaStream_t st, int batch, int m, int n, int k, float2 alpha, const float2* A, int lda,
+                         long long sA, const float2* B, int ldb, long long sB, float beta, float2* C, int ldc,
+                         long long sC, int* err);
+cudaError_t getrf_f32_tc(cudaStream_t st, float2* M, int nb, int K, int* piv, int* info, int* err);
+cudaError_t getrs_f32_tc(cudaStream_t st, const float2* LU, const int* piv, int nb, int K, const double2* B, int nrhs,
+                         float2* X, int* perm, int* err);
+cudaError_t getrs_f32_tc(cudaStream_t st, const float2* LU, const int* piv, int nb, int K, const float2* B, int nrhs,
+                         float2* X, int* perm, int* err);
+int tc_panel();
+
 // Dyson / transmission launchers (dyson.cu).
 rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR, int K, void* G, double* refres);
 rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL, const void* SR, int K, void* G,

@@ -24,7 +24,7 @@ def lib(repo_root):
 def _declared(repo_root):
     hdr = open(os.path.join(repo_root, "include", "rsfd.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(rsfd_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(rsfd_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def test_exports_every_declared_symbol(lib, repo_root):
