@@ -619,6 +619,9 @@ struct PassParams {
   int depth;                 // TMA bundles in flight ahead of the consumers (1 .. kMaxDepth)
   int stored_u;              // 1: the pass reads the stored A r_{n-1} (seed switches fold the energy
                              //    shift of the stored product into a1)
+  int has_proj;              // 1: nonlocal projectors; the pass leaves its dots in pdots and the
+                             //    projector kernel finishes A r_n, the dots and the scalar step
+  double* pdots;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -1099,7 +1102,20 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
 
   double v5[5];
   acc.get(v5);
-  if (pass_finish(p, slot, cta, v5, S, s_last)) scalar_step(p, slot, S);
+  if (pass_finish(p, slot, cta, v5, S, s_last)) {
+    if (p.has_proj) {
+      if (threadIdx.x == 0) {
+        double* o = p.pdots + (size_t)slot * 8;
+        o[0] = S.rr.x;
+        o[1] = S.rr.y;
+        o[2] = S.rAr.x;
+        o[3] = S.rAr.y;
+        o[4] = S.nrm2;
+      }
+    } else {
+      scalar_step(p, slot, S);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1410,7 +1426,188 @@ __global__ void __launch_bounds__(MaxThreadsU<P>::value) passu_kernel(PassParams
   }
   double v5[5];
   acc.get(v5);
-  if (pass_finish(p, slot, cta, v5, S, s_last)) scalar_step(p, slot, S);
+  if (pass_finish(p, slot, cta, v5, S, s_last)) {
+    if (p.has_proj) {
+      if (threadIdx.x == 0) {
+        double* o = p.pdots + (size_t)slot * 8;
+        o[0] = S.rr.x;
+        o[1] = S.rr.y;
+        o[2] = S.rAr.x;
+        o[3] = S.rAr.y;
+        o[4] = S.nrm2;
+      }
+    } else {
+      scalar_step(p, slot, S);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// nonlocal projector term (separable Kleinman-Bylander form, Sec. II A):
+//   V_nl r = sum_a E_a c_a p_a,   c_a = h^3 p_a^T r,
+// so with u_loc = (Z_s - H_loc) r from the pass,
+//   A r = u_loc - sum_a E_a c_a p_a,   (r, A r) = (r, u_loc) - sum_a E_a c_a^2 / h^3.
+// proj_kernel: one block per (atom, slot) forms c_a (a gather-GEMV over the atom's support, exact
+// products in double-float or FP64), stores -E_a c_a and the dot correction; the last block of a
+// slot (atomic ticket) sums the corrections in atom order and runs the FP64 scalar step.
+// pscatter_kernel: u_n -= sum_a E_a c_a p_a over the union of the supports, one thread per support
+// point gathering its atoms (point-major CSR), so no atomics and a fixed summation order.
+// ------------------------------------------------------------------------------------------------
+struct ProjParams {
+  PassParams pp;
+  int n_atoms, n_supp;
+  const int* a_ptr;
+  const long long* a_idx;
+  const void* a_val;
+  const double* a_E;
+  const int* t_ptr;
+  const long long* t_pidx;
+  const int* t_atom;
+  const void* t_val;
+  double h3;
+  double2* pw;
+  double2* pcorr;
+  unsigned int* ptickets;
+};
+
+// per-thread FP64 sum of p_j r_j, per precision
+template <int MODE> struct ProjAcc;
+template <> struct ProjAcc<RSFD_FP64> {
+  double2 s = make_double2(0.0, 0.0);
+  __device__ __forceinline__ void add(double pv, double2 r) {
+    s.x = fma(pv, r.x, s.x);
+    s.y = fma(pv, r.y, s.y);
+  }
+  __device__ __forceinline__ double2 get() const { return s; }
+};
+template <> struct ProjAcc<RSFD_MIXED> {
+  double2 s = make_double2(0.0, 0.0);
+  __device__ __forceinline__ void add(float pv, float2 r) {
+    s.x = fma((double)pv, (double)r.x, s.x);
+    s.y = fma((double)pv, (double)r.y, s.y);
+  }
+  __device__ __forceinline__ double2 get() const { return s; }
+};
+template <> struct ProjAcc<RSFD_DF64> {
+  DFAcc a = dfacc_zero();
+  __device__ __forceinline__ void add(float2 pv, const dfc& r) {
+    dfr c;
+    c.h = pv.x;
+    c.l = pv.y;
+    dfacc_mul(a, c, r);
+  }
+  __device__ __forceinline__ double2 get() const {
+    return make_double2((double)a.s.x + (double)a.lo.x, (double)a.s.y + (double)a.lo.y);
+  }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) proj_kernel(ProjParams q) {
+  typedef typename Ops<MODE>::C C;
+  typedef typename Ops<MODE>::VT VT;
+  __shared__ ScalarShared S;
+  __shared__ int s_last;
+  const PassParams& p = q.pp;
+  const int a = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
+  SlotState* st = p.slots + slot;
+  if (st->status != SLOT_RUNNING) return;
+  const int n = st->n;   // the pass of this iteration wrote r_n to ring entry n % 3
+  const long long vec = (long long)p.d.nz * p.d.ny * p.d.nxp;
+  const C* r = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * p.d.nvec + n % 3) * vec;
+  const VT* pv = reinterpret_cast<const VT*>(q.a_val);
+  ProjAcc<MODE> acc;
+  for (int e = q.a_ptr[a] + tid; e < q.a_ptr[a + 1]; e += blockDim.x) acc.add(pv[e], r[q.a_idx[e]]);
+  const double2 t = acc.get();
+  double v2[2] = {warp_sum(t.x), warp_sum(t.y)};
+  block_sum_lane0<2>(v2, S.red);
+  if (tid == 0) {
+    const double2 c = make_double2(v2[0] * q.h3, v2[1] * q.h3);
+    const double E = q.a_E[a];
+    q.pw[(size_t)slot * q.n_atoms + a] = make_double2(-E * c.x, -E * c.y);
+    const double2 c2 = cmul(c, c);
+    q.pcorr[(size_t)slot * q.n_atoms + a] = make_double2(E * c2.x / q.h3, E * c2.y / q.h3);
+    __threadfence();
+    const unsigned int tk = atomicAdd(q.ptickets + slot, 1u);
+    s_last = (tk == (unsigned int)(q.n_atoms - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid < 32) {
+    double cx = 0.0, cy = 0.0;
+    const double2* src = q.pcorr + (size_t)slot * q.n_atoms;
+    for (int k = tid; k < q.n_atoms; k += 32) {
+      const double2 v = __ldcg(src + k);
+      cx += v.x;
+      cy += v.y;
+    }
+    cx = warp_sum(cx);
+    cy = warp_sum(cy);
+    if (tid == 0) {
+      const double* dd = p.pdots + (size_t)slot * 8;
+      S.rr = make_double2(__ldcg(dd + 0), __ldcg(dd + 1));
+      S.rAr = make_double2(__ldcg(dd + 2) - cx, __ldcg(dd + 3) - cy);
+      S.nrm2 = __ldcg(dd + 4);
+      q.ptickets[slot] = 0u;
+    }
+  }
+  __syncthreads();
+  scalar_step(p, slot, S);
+}
+
+// u (vector element) += pv * w for a real projector value pv and a complex FP64 coefficient w
+__device__ __forceinline__ void scat_add(double2& u, double pv, double2 w) {
+  u.x = fma(pv, w.x, u.x);
+  u.y = fma(pv, w.y, u.y);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) pscatter_kernel(ProjParams q) {
+  typedef typename Ops<MODE>::C C;
+  typedef typename Ops<MODE>::VT VT;
+  const PassParams& p = q.pp;
+  const int slot = blockIdx.y;
+  SlotState* st = p.slots + slot;
+  if (st->status != SLOT_RUNNING) return;
+  const int n = st->n - 1;   // the scalar step of this iteration advanced n
+  const long long vec = (long long)p.d.nz * p.d.ny * p.d.nxp;
+  C* u = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * p.d.nvec + 3 + n % 2) * vec;
+  const VT* tv = reinterpret_cast<const VT*>(q.t_val);
+  const double2* w = q.pw + (size_t)slot * q.n_atoms;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < q.n_supp; s += gridDim.x * blockDim.x) {
+    const long long gi = q.t_pidx[s];
+    if (MODE == RSFD_DF64) {
+      const dfc u0 = *reinterpret_cast<const dfc*>(&u[gi]);
+      DFAcc acc = dfacc_from(u0);
+      for (int e = q.t_ptr[s]; e < q.t_ptr[s + 1]; ++e) {
+        const double2 ww = w[q.t_atom[e]];
+        const float2 pf = *reinterpret_cast<const float2*>(&tv[e]);
+        dfc wc;
+        wc.h = make_float2((float)ww.x, (float)ww.y);
+        wc.l = make_float2((float)(ww.x - (double)wc.h.x), (float)(ww.y - (double)wc.h.y));
+        dfr c;
+        c.h = pf.x;
+        c.l = pf.y;
+        dfacc_mul(acc, c, wc);
+      }
+      *reinterpret_cast<dfc*>(&u[gi]) = dfacc_get(acc);
+    } else {
+      double2 uu;
+      if (MODE == RSFD_FP64) {
+        uu = *reinterpret_cast<const double2*>(&u[gi]);
+      } else {
+        const float2 uf = *reinterpret_cast<const float2*>(&u[gi]);
+        uu = make_double2((double)uf.x, (double)uf.y);
+      }
+      for (int e = q.t_ptr[s]; e < q.t_ptr[s + 1]; ++e) {
+        const double pd = (MODE == RSFD_FP64) ? (double)*reinterpret_cast<const double*>(&tv[e])
+                                              : (double)*reinterpret_cast<const float*>(&tv[e]);
+        scat_add(uu, pd, w[q.t_atom[e]]);
+      }
+      if (MODE == RSFD_FP64) *reinterpret_cast<double2*>(&u[gi]) = uu;
+      else *reinterpret_cast<float2*>(&u[gi]) = make_float2((float)uu.x, (float)uu.y);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1637,6 +1834,8 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.hist_len = hist_len;
   p.depth = d.depth;
   p.stored_u = d.kind == RSFD_PASS_STORED;
+  p.has_proj = b.n_atoms > 0;
+  p.pdots = b.pdots;
   dim3 grid(d.ctas_per_slot, d.W);
   if (d.kind == RSFD_PASS_STORED) {
     const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth);
@@ -1714,6 +1913,68 @@ cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, co
                     : launch_pass_t<RSFD_MIXED, 2>(d, b, c, tol, maxit, hist_len, st);
   return d.R == 1 ? launch_pass_t<RSFD_DF64, 1>(d, b, c, tol, maxit, hist_len, st)
                   : launch_pass_t<RSFD_DF64, 2>(d, b, c, tol, maxit, hist_len, st);
+}
+
+template <int MODE, int R>
+cudaError_t launch_proj_t(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
+                          int hist_len, cudaStream_t st) {
+  ProjParams q;
+  PassParams& p = q.pp;
+  p.d = d;
+  p.rbuf = b.rbuf;
+  p.V = b.V;
+  p.rhist = b.rhist;
+  p.slots = b.slots;
+  p.shifts = b.shifts;
+  p.coef = b.coef;
+  p.partials = b.partials;
+  p.tickets = b.tickets;
+  p.Z = b.Z;
+  p.counters = b.counters;
+  p.error_flag = b.error_flag;
+  p.hd = c.hd;
+  p.hk1 = c.hk[0];
+  p.hk2 = (R == 2) ? c.hk[1] : 0.0;
+  p.tol = tol;
+  p.maxit = maxit;
+  p.hist_len = hist_len;
+  p.depth = d.depth;
+  p.stored_u = 1;
+  p.has_proj = 1;
+  p.pdots = b.pdots;
+  q.n_atoms = b.n_atoms;
+  q.n_supp = b.n_supp;
+  q.a_ptr = b.a_ptr;
+  q.a_idx = b.a_idx;
+  q.a_val = b.a_val;
+  q.a_E = b.a_E;
+  q.t_ptr = b.t_ptr;
+  q.t_pidx = b.t_pidx;
+  q.t_atom = b.t_atom;
+  q.t_val = b.t_val;
+  q.h3 = b.h3;
+  q.pw = b.pw;
+  q.pcorr = b.pcorr;
+  q.ptickets = b.ptickets;
+  proj_kernel<MODE><<<dim3(b.n_atoms, d.W), 256, 0, st>>>(q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int gx = (b.n_supp + 255) / 256;
+  pscatter_kernel<MODE><<<dim3(gx < 1 ? 1 : gx, d.W), 256, 0, st>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proj(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
+                        int maxit, int hist_len, cudaStream_t st) {
+  if (b.n_atoms <= 0) return cudaSuccess;
+  if (prec == RSFD_FP64)
+    return d.R == 1 ? launch_proj_t<RSFD_FP64, 1>(d, b, c, tol, maxit, hist_len, st)
+                    : launch_proj_t<RSFD_FP64, 2>(d, b, c, tol, maxit, hist_len, st);
+  if (prec == RSFD_MIXED)
+    return d.R == 1 ? launch_proj_t<RSFD_MIXED, 1>(d, b, c, tol, maxit, hist_len, st)
+                    : launch_proj_t<RSFD_MIXED, 2>(d, b, c, tol, maxit, hist_len, st);
+  return d.R == 1 ? launch_proj_t<RSFD_DF64, 1>(d, b, c, tol, maxit, hist_len, st)
+                  : launch_proj_t<RSFD_DF64, 2>(d, b, c, tol, maxit, hist_len, st);
 }
 
 cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, int hist_len, cudaStream_t st) {

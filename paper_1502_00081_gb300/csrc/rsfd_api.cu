@@ -44,13 +44,19 @@ struct Handle {
   int nr = 0;                  // recorded rows: nb + track.size() * Nx * Ny
   void* dV = nullptr;
   int64_t* dbrow = nullptr;
-  // nonlocal projectors (host copy; the device path for them is not built yet)
-  int n_atoms = 0;
+  // nonlocal projectors: atom-major and point-major CSR of the same entries on the device
+  int n_atoms = 0, n_supp = 0;
+  long long nnz = 0;
+  int *d_aptr = nullptr, *d_tptr = nullptr, *d_tatom = nullptr;
+  long long *d_aidx = nullptr, *d_tpidx = nullptr;
+  void *d_aval = nullptr, *d_tval = nullptr;
+  double* d_aE = nullptr;
   rsfd_solve_opts opts;
   rsfd_stats stats;
   std::string err = "no error";
   // solver workspace
   DevBuf rbuf, xbuf, pbuf, rhist, coef, eflag, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
+  DevBuf pw, pcorr, pdots, ptickets;   // projector term of the solve
   CUtensorMap tmR, tmV;
   // dyson / transmission workspace
   DevBuf dy[8];
@@ -119,7 +125,8 @@ rsfd_status handle_end(Handle* h) {
 static void free_all(Handle* h) {
   DevBuf* bufs[] = {&h->rbuf,  &h->xbuf,      &h->pbuf,      &h->rhist,    &h->coef,
                     &h->eflag, &h->slots,     &h->shifts,    &h->partials, &h->tickets,
-                    &h->Z,     &h->init_list, &h->init_grid, &h->counters};
+                    &h->Z,     &h->init_list, &h->init_grid, &h->counters, &h->pw,
+                    &h->pcorr, &h->pdots,     &h->ptickets};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -132,6 +139,13 @@ static void free_all(Handle* h) {
   }
   if (h->dV) cudaFree(h->dV);
   if (h->dbrow) cudaFree(h->dbrow);
+  void* pj[] = {h->d_aptr, h->d_tptr, h->d_tatom, h->d_aidx, h->d_tpidx, h->d_aval, h->d_tval, h->d_aE};
+  for (void* q : pj)
+    if (q) cudaFree(q);
+  h->d_aptr = h->d_tptr = h->d_tatom = nullptr;
+  h->d_aidx = h->d_tpidx = nullptr;
+  h->d_aval = h->d_tval = nullptr;
+  h->d_aE = nullptr;
   h->dV = nullptr;
   h->dbrow = nullptr;
 }
@@ -277,7 +291,21 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   const long long N = (long long)grid[0] * grid[1] * grid[2];
   if (N > (1ll << 31) - 1) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: grid too large (N >= 2^31)");
   if (proj && proj->n_atoms > 0) {
-    return fail(nullptr, RSFD_ERR_UNSUPPORTED, "rsfd_create: nonlocal projectors are not supported by this build");
+    if (!proj->ptr || !proj->idx || !proj->val || !proj->E)
+      return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: projector arrays must be non-NULL");
+    if (proj->ptr[0] != 0) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: projector ptr[0] must be 0");
+    for (int a = 0; a < proj->n_atoms; ++a) {
+      if (proj->ptr[a + 1] < proj->ptr[a]) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: projector ptr not monotone");
+      if (!isfinite(proj->E[a])) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: non-finite projector energy");
+    }
+    const long long nnz = proj->ptr[proj->n_atoms];
+    if (nnz > (1ll << 31) - 1) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: too many projector entries");
+    for (long long e = 0; e < nnz; ++e) {
+      if (proj->idx[e] < 0 || proj->idx[e] >= N) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: projector index out of range");
+      if (!isfinite(proj->val[e])) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: non-finite projector value");
+    }
+  } else if (proj && proj->n_atoms < 0) {
+    return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: negative n_atoms");
   }
   for (long long i = 0; i < N; ++i) {
     if (!isfinite(V_loc[i])) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: V_loc has a non-finite entry");
@@ -347,6 +375,76 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   }
   if (e == cudaSuccess) e = cudaMemcpy(h->dbrow, h->brow.data(), h->nb * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  if (proj && proj->n_atoms > 0) {
+    // atom-major entries (padded vector indices, values in the potential's element type) and the
+    // point-major transpose of the same entries (support points in ascending order, atoms ascending)
+    const int na = proj->n_atoms;
+    const long long nnz = proj->ptr[na];
+    auto pad = [&](long long j) {
+      const long long z = j / nxy, r = j - z * nxy, y = r / h->nx, x = r - y * h->nx;
+      return (z * h->ny + y) * h->nxp + x;
+    };
+    auto put = [&](std::vector<unsigned char>& buf, long long q, double v) {
+      if (precision == RSFD_FP64) {
+        ((double*)buf.data())[q] = v;
+      } else if (precision == RSFD_MIXED) {
+        ((float*)buf.data())[q] = (float)v;
+      } else {
+        const float hi = (float)v;
+        ((float*)buf.data())[2 * q] = hi;
+        ((float*)buf.data())[2 * q + 1] = (float)(v - (double)hi);
+      }
+    };
+    std::vector<int> aptr(na + 1);
+    std::vector<long long> aidx(nnz);
+    std::vector<unsigned char> aval(nnz * vsz + 16);
+    std::vector<std::pair<long long, int>> ent(nnz);   // (grid index, atom) of every entry
+    for (int a = 0; a <= na; ++a) aptr[a] = (int)proj->ptr[a];
+    for (int a = 0; a < na; ++a)
+      for (long long e2 = proj->ptr[a]; e2 < proj->ptr[a + 1]; ++e2) {
+        aidx[e2] = pad(proj->idx[e2]);
+        put(aval, e2, proj->val[e2]);
+        ent[e2] = std::make_pair(proj->idx[e2], a);
+      }
+    std::vector<long long> order(nnz);
+    for (long long e2 = 0; e2 < nnz; ++e2) order[e2] = e2;
+    std::stable_sort(order.begin(), order.end(), [&](long long u, long long v) { return ent[u] < ent[v]; });
+    std::vector<int> tptr, tatom(nnz);
+    std::vector<long long> tpidx;
+    std::vector<unsigned char> tval(nnz * vsz + 16);
+    for (long long k = 0; k < nnz; ++k) {
+      const long long e2 = order[k];
+      if (k == 0 || ent[e2].first != ent[order[k - 1]].first) {
+        tptr.push_back((int)k);
+        tpidx.push_back(pad(ent[e2].first));
+      }
+      tatom[k] = ent[e2].second;
+      put(tval, k, proj->val[e2]);
+    }
+    tptr.push_back((int)nnz);
+    h->n_atoms = na;
+    h->nnz = nnz;
+    h->n_supp = (int)tpidx.size();
+    e = cudaMalloc((void**)&h->d_aptr, (na + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_aidx, (nnz + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_aval, nnz * vsz + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_aE, na * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tptr, tptr.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tpidx, (tpidx.size() + 1) * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tatom, (nnz + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_tval, nnz * vsz + 16);
+    if (e != cudaSuccess) return bail(RSFD_ERR_ALLOC, std::string("rsfd_create: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(h->d_aptr, aptr.data(), (na + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_aidx, aidx.data(), nnz * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_aval, aval.data(), nnz * vsz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_aE, proj->E, na * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tptr, tptr.data(), tptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_tpidx, tpidx.data(), tpidx.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tatom, tatom.data(), nnz * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_tval, tval.data(), nnz * vsz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  }
   *out = h;
   return RSFD_OK;
 }
@@ -399,6 +497,8 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
   if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_STORED)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: bad pass_kind");
+  if (o->pass_kind == RSFD_PASS_RECOMPUTE && h->n_atoms > 0)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the recompute pass has no projector term; use the stored pass");
   if (o->rows_per_thread != 0 && o->rows_per_thread != 1 && o->rows_per_thread != 2 && o->rows_per_thread != 4)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: rows_per_thread must be 0, 1, 2 or 4");
   const int rows = resolve_rows(o->rows_per_thread);
@@ -469,6 +569,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.K = K;
   d.ncols = ncols;
   d.kind = resolve_kind(prec, h->opts.pass_kind);
+  if (h->n_atoms > 0) d.kind = RSFD_PASS_STORED;   // the projector term follows the stored-product pass
   d.nvec = d.kind == RSFD_PASS_STORED ? 5 : 3;
   d.rows = resolve_rows(h->opts.rows_per_thread);
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
@@ -561,6 +662,27 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   b.init_list = (int*)h->init_list.p;
   b.init_grid = (long long*)h->init_grid.p;
   b.counters = (unsigned long long*)h->counters.p;
+  if (h->n_atoms > 0) {
+    if ((s = ensure(h, h->pw, (size_t)W * h->n_atoms * sizeof(double2))) != RSFD_OK) return s;
+    if ((s = ensure(h, h->pcorr, (size_t)W * h->n_atoms * sizeof(double2))) != RSFD_OK) return s;
+    if ((s = ensure(h, h->pdots, (size_t)W * 8 * sizeof(double))) != RSFD_OK) return s;
+    if ((s = ensure(h, h->ptickets, (size_t)W * sizeof(unsigned int))) != RSFD_OK) return s;
+    b.n_atoms = h->n_atoms;
+    b.n_supp = h->n_supp;
+    b.a_ptr = h->d_aptr;
+    b.a_idx = h->d_aidx;
+    b.a_val = h->d_aval;
+    b.a_E = h->d_aE;
+    b.t_ptr = h->d_tptr;
+    b.t_pidx = h->d_tpidx;
+    b.t_atom = h->d_tatom;
+    b.t_val = h->d_tval;
+    b.h3 = h->h * h->h * h->h;
+    b.pw = (double2*)h->pw.p;
+    b.pcorr = (double2*)h->pcorr.p;
+    b.pdots = (double*)h->pdots.p;
+    b.ptickets = (unsigned int*)h->ptickets.p;
+  }
   const StencilCoef coef = stencil_coef(h->fd_order, h->h);
 
   if ((s = handle_begin(h)) != RSFD_OK) return s;
@@ -574,6 +696,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   for (int k = 0; k < K; ++k) Zh[k] = make_double2(energies[k], eta);
   RSFD_CK(h, cudaMemcpyAsync(b.Z, Zh.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
   RSFD_CK(h, cudaMemsetAsync(b.tickets, 0, W * sizeof(unsigned int), st));
+  if (b.n_atoms > 0) RSFD_CK(h, cudaMemsetAsync(b.ptickets, 0, W * sizeof(unsigned int), st));
   RSFD_CK(h, cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned long long), st));
   RSFD_CK(h, cudaMemsetAsync(b.error_flag, 0, sizeof(int), st));
   std::vector<SlotState> hs(W);
@@ -637,6 +760,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
     for (int t = 0; t < C; ++t) {
       if (h->opts.profile) RSFD_CK(h, rec(pev[t]));
       RSFD_CK(h, launch_pass(prec, d, b, coef, tol, maxit, C, st));
+      if (b.n_atoms > 0) RSFD_CK(h, launch_proj(prec, d, b, coef, tol, maxit, C, st));
     }
     if (h->opts.profile) RSFD_CK(h, rec(pev[C]));
     RSFD_CK(h, launch_chunk(prec, d, b, C, st));
@@ -662,7 +786,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
     }
     h->stats.n_pass += C;
     h->stats.n_shift += 1;
-    h->stats.n_other += 1;
+    h->stats.n_other += 1 + (b.n_atoms > 0 ? 2 * C : 0);
     RSFD_CK(h, cudaMemcpyAsync(hs.data(), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
     RSFD_CK(h, cudaMemcpyAsync(&herr, b.error_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     RSFD_CK(h, cudaStreamSynchronize(st));

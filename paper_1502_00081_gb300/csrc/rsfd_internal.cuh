@@ -135,6 +135,22 @@ struct SolverBuffers {
   int* init_list;         // [W][2]: slot, column c
   long long* init_grid;   // [W]: grid index j of the new column
   unsigned long long* counters;  // [0] active (slot, energy) updates, [1] slot iterations
+  // nonlocal projectors (n_atoms == 0: none), V_nl r = sum_a E_a c_a p_a with c_a = h^3 p_a^T r
+  int n_atoms;
+  int n_supp;             // grid points in the union of the projector supports
+  const int* a_ptr;       // [n_atoms + 1] atom-major CSR
+  const long long* a_idx; // [nnz] padded vector index of each entry
+  const void* a_val;      // [nnz] projector values (potential element type)
+  const double* a_E;      // [n_atoms] projector energies
+  const int* t_ptr;       // [n_supp + 1] point-major CSR of the same entries
+  const long long* t_pidx;// [n_supp] padded vector index of each support point
+  const int* t_atom;      // [nnz] atom of each point-major entry
+  const void* t_val;      // [nnz] its projector value
+  double h3;
+  double2* pw;            // [W][n_atoms] -E_a c_a of the last pass
+  double2* pcorr;         // [W][n_atoms] E_a c_a^2 / h^3
+  double* pdots;          // [W][8] (r,r), (r, u_loc), ||r||^2 of the last pass
+  unsigned int* ptickets; // [W]
 };
 
 struct StencilCoef {
@@ -148,6 +164,10 @@ struct PassConfig {
 
 // Launch one fused pass (stencil + seed update + dots + scalar step) over all slots.
 cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
+                        int maxit, int hist_len, cudaStream_t st);
+// Nonlocal projector term after a pass (stored-product form only): projections c_a = h^3 p_a^T r_n,
+// the corrected (r_n, A r_n) and the FP64 scalar step, then u_n -= sum_a E_a c_a p_a.
+cudaError_t launch_proj(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
                         int maxit, int hist_len, cudaStream_t st);
 // Apply the collapsed shift update of the recorded history of every slot, then clear the history.
 cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, int hist_len, cudaStream_t st);
