@@ -235,7 +235,7 @@ def run_gpu(args):
     cols = batches[0]
     prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[p.precision]
     vsz = 8 if prec == rs.RSFD_MIXED else 16
-    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
+    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, proj=p.proj, precision=prec)
     rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, tile_y=args.tile_y,
                               z_chunk=args.z_chunk, profile=1)
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
@@ -292,11 +292,15 @@ def run_gpu(args):
     dom = max(kern, key=lambda k: kern[k][1])
     dbytes, dms = kern[dom]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else None
+    # measured DRAM bytes (ncu, one launch of this kernel on this workload and precision), stored per
+    # slot-iteration and scaled to this run's average launch
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and agg["n_pass"] > 0:
         try:
-            traffic = json.load(open(tfile)).get(dom)
+            t = json.load(open(tfile)).get(dom)
+            if t and t.get("workload") == p.name and t.get("precision") == p.precision:
+                traffic = t["bytes_per_slot_iteration"] * agg["slot_iterations"] / agg["n_pass"]
         except Exception:
             traffic = None
 
@@ -311,7 +315,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e_steps):
-            h2 = rs.Handle(p.grid, p.h, p.fd_order, Vh.numpy(), n_face=p.n_face, precision=prec)
+            h2 = rs.Handle(p.grid, p.h, p.fd_order, Vh.numpy(), n_face=p.n_face, proj=p.proj, precision=prec)
             rs.rsfd_set_solve_options(h2.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync)
             G2 = torch.empty_like(G0)
             rs.rsfd_shifted_cocg(h2.ptr, cols, p.energies, p.eta, p.tol, p.maxit, G2)
@@ -404,7 +408,7 @@ def run_shift_scaling(args):
     p = make_problem(args.workload)
     prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[args.precision]
     cols = p.cols[:args.ncols or 8]
-    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
+    h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, proj=p.proj, precision=prec)
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
 
     def solve(E):
@@ -491,6 +495,90 @@ def run_precision_speedup(args):
                               "speedup_vs_fp64": (base / tot) if ok and base else None}), flush=True)
 
 
+def run_dyson_scaling(args):
+    """The Dyson step (Eq. sec3-01a on the boundary rows) alone, tensor-core form (FP32 LU and
+    triangular solves with 3xTF32 tcgen05 updates, FP64 residual refinement) against the FP64
+    CUDA-core form, on seeded random complex-symmetric G0_bb and retarded Sigma of the boundary
+    sizes of the workloads: nb = 1024, 2048 (both forms) and 4608, 9216 (the 48 x 48 plane and
+    two-plane slab of the full-boundary workload; tensor-core form only, one energy).  One JSON
+    line per (nb, form): seconds per energy, the FP64 refinement residual, and the difference
+    between the two forms where both ran."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import random_complex_matrices
+    torch.cuda.set_device(0)
+    rs.load_library()
+
+    def abi(M):
+        return torch.from_numpy(np.ascontiguousarray(M.transpose(0, 2, 1))).cuda()
+
+    for nb, K, forms in ((1024, 4, ("tc", "fp64")), (2048, 2, ("tc", "fp64")), (4608, 1, ("tc",)),
+                         (9216, 1, ("tc",))):
+        if args.dyson_max_nb and nb > args.dyson_max_nb:
+            continue
+        G0 = abi(random_complex_matrices(nb, K, seed=41, scale=0.5))
+        SL = abi(random_complex_matrices(nb // 2, K, seed=42, scale=0.5, imag_sign=-1))
+        SR = abi(random_complex_matrices(nb // 2, K, seed=43, scale=0.5, imag_sign=-1))
+        out = {}
+        for form in forms:
+            kind = rs.RSFD_DYSON_TC if form == "tc" else rs.RSFD_DYSON_FP64
+            with rs.Handle((nb // 2, 1, 4), 0.5, 2, np.zeros(nb // 2 * 4), n_face=1, precision=rs.RSFD_DF64) as h:
+                rs.rsfd_set_solve_options(h.ptr, dyson_kind=kind, dyson_refine=1 if form == "tc" else 2)
+                G = torch.empty((K, nb, nb), dtype=torch.complex128, device="cuda")
+                if nb <= 2048:
+                    rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)   # warm-up (workspace, module load)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ref = rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                out[form] = G
+                nref = 1 if form == "tc" else 2
+                line = {"experiment": "dyson_scaling", "form": form, "nb": nb, "energies": K,
+                        "seconds_per_energy": dt / K, "refine_steps": nref,
+                        "max_refine_residual": float(ref.max()),
+                        "fp64_flops_per_energy": (4 + 8 * (nref + 1)) * nb ** 3 if form == "tc" else None,
+                        "tf32_flops_per_energy": 3 * (8.0 / 3 + 8 * (nref + 1)) * nb ** 3 if form == "tc" else None}
+                if form == "fp64" and "tc" in out:
+                    d = torch.linalg.norm(out["tc"] - G) / torch.linalg.norm(G)
+                    line["rel_diff_tc_vs_fp64"] = float(d)
+                print(json.dumps(line), flush=True)
+        del G0, SL, SR, out
+        torch.cuda.empty_cache()
+
+
+def run_tc_gemm(args):
+    """The tensor-core GEMM of the Dyson step (rsfd_cgemm_tf32x3: complex FP32, 3xTF32 on tcgen05)
+    alone, on the shapes it meets: a square 4096^3 product and the K = 64 panel updates of the
+    blocked LU and triangular solves.  Reports complex FLOP/s (8 m n k per product) and the issued
+    TF32 rate (three real-split products of four real GEMMs: 3 x 8 m n k)."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    torch.cuda.set_device(0)
+    rs.load_library()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    shapes = ((1, 4096, 4096, 4096), (4, 2048, 2048, 128), (16, 1024, 1024, 64), (8, 4096, 4096, 64))
+    for (b, m, n, k) in shapes:
+        if args.gemm_size and m != args.gemm_size:
+            continue
+        A = torch.randn(b, k, m, dtype=torch.complex64, device="cuda", generator=g)
+        B = torch.randn(b, n, k, dtype=torch.complex64, device="cuda", generator=g)
+        C = torch.zeros(b, n, m, dtype=torch.complex64, device="cuda")
+        rs.rsfd_cgemm_tf32x3(A, B, C, alpha=-1.0, beta=1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            rs.rsfd_cgemm_tf32x3(A, B, C, alpha=-1.0, beta=1.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        fl = 8.0 * b * m * n * k
+        print(json.dumps({"experiment": "tc_gemm", "batch": b, "m": m, "n": n, "k": k, "ms": ms,
+                          "complex_tflops": fl / ms / 1e9, "tf32_tflops_issued": 3 * fl / ms / 1e9}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,7 +587,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="df64", choices=["mixed", "fp64", "df64"])
-    ap.add_argument("--cols-per-step", type=int, default=32, help="columns solved per step (0 = the whole sample)")
+    ap.add_argument("--cols-per-step", type=int, default=38,
+                    help="columns solved per step (0 = the whole sample); 38 columns x 32 CTAs per column fill "
+                         "exactly four waves of the 152 SMs x 2 resident CTAs")
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap per column (profiling runs)")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--z-chunk", type=int, default=0)
@@ -510,8 +600,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--experiment", default=None, choices=[None, "shift_scaling", "precision_speedup"],
+    ap.add_argument("--experiment", default=None,
+                    choices=[None, "shift_scaling", "precision_speedup", "dyson_scaling", "tc_gemm"],
                     help="run an experiment instead of the benchmark (JSON lines)")
+    ap.add_argument("--dyson-max-nb", type=int, default=0, help="dyson_scaling: largest boundary size (0 = all)")
+    ap.add_argument("--gemm-size", type=int, default=0, help="tc_gemm: only the shapes with this m (0 = all)")
     ap.add_argument("--max-independent", type=int, default=32,
                     help="shift_scaling: largest K also solved as K independent single-energy solves")
     args = ap.parse_args()
@@ -520,6 +613,12 @@ def main():
         return
     if args.experiment == "precision_speedup":
         run_precision_speedup(args)
+        return
+    if args.experiment == "dyson_scaling":
+        run_dyson_scaling(args)
+        return
+    if args.experiment == "tc_gemm":
+        run_tc_gemm(args)
         return
     if args.impl == "reference":
         run_reference(args)

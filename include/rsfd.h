@@ -132,7 +132,8 @@ typedef struct {
   int32_t prefetch;       /* z-planes of input the pass keeps in flight (TMA), 1..7 */
   int32_t rows_per_thread;/* RSFD_PASS_STORED: tile rows per thread, 1, 2 or 4 (tile_y must be a multiple) */
   int32_t dyson_kind;     /* rsfd_dyson_kind of rsfd_dyson_boundary */
-  int32_t dyson_refine;   /* FP64 refinement steps of rsfd_dyson_boundary (0 = 2; at most 8) */
+  int32_t dyson_refine;   /* FP64 refinement steps of rsfd_dyson_boundary (0 = 2 for FP64 handles, 1 for
+                             double-float and complex64 handles; at most 8) */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */
@@ -157,7 +158,10 @@ typedef struct {
  *   n_face    = planes per side in the boundary row set b, 1 <= n_face <= Nz/2;
  *               0 selects fd_order/2 (the planes the lead couples to).
  *   V_loc     = host [N] local potential, linear grid order.
- *   proj      = NULL or the nonlocal projectors (host arrays, copied).
+ *   proj      = NULL or the nonlocal projectors (host arrays, copied; entries of one atom at distinct
+ *               grid points).  With projectors the solver always uses the stored-product pass: after
+ *               each pass a projection kernel forms c_a = h^3 p_a^T r_n, corrects (r_n, A r_n) and runs
+ *               the scalar step, and a scatter kernel adds -sum_a E_a c_a p_a to A r_n.
  *   precision = RSFD_FP64, RSFD_MIXED or RSFD_DF64.
  *   stream    = cudaStream_t for every device operation of this handle.
  * Returns RSFD_ERR_ARG on invalid sizes, RSFD_ERR_ALLOC / RSFD_ERR_CUDA on

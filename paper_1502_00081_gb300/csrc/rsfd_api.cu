@@ -105,7 +105,10 @@ int handle_dyson_kind(Handle* h) {
   if (h->opts.dyson_kind != RSFD_DYSON_AUTO) return h->opts.dyson_kind;
   return h->prec == RSFD_FP64 ? RSFD_DYSON_FP64 : RSFD_DYSON_TC;
 }
-int handle_dyson_refine(Handle* h) { return h->opts.dyson_refine > 0 ? h->opts.dyson_refine : 2; }
+int handle_dyson_refine(Handle* h) {
+  if (h->opts.dyson_refine > 0) return h->opts.dyson_refine;
+  return h->prec == RSFD_FP64 ? 2 : 1;
+}
 rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& m) { return fail(h, s, m); }
 
 // order the internal stream after the caller's stream
