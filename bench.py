@@ -238,6 +238,12 @@ def run_gpu(args):
     h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, proj=p.proj, precision=prec)
     rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, tile_y=args.tile_y,
                               z_chunk=args.z_chunk, profile=1)
+    tuned = None
+    if not args.no_autotune:
+        # launch options picked by the library's autotuner for this block width (not timed)
+        topts, tus = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(cols.size), iters=256)
+        tuned = {"pass_kind": topts["pass_kind"], "tile_y": topts["tile_y"], "rows_per_thread": topts["rows_per_thread"],
+                 "z_chunk": topts["z_chunk"], "iters_per_sync": topts["iters_per_sync"], "us_per_slot_iteration": tus}
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -317,6 +323,8 @@ def run_gpu(args):
         for _ in range(e_steps):
             h2 = rs.Handle(p.grid, p.h, p.fd_order, Vh.numpy(), n_face=p.n_face, proj=p.proj, precision=prec)
             rs.rsfd_set_solve_options(h2.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync)
+            if not args.no_autotune:
+                rs.rsfd_autotune(h2.ptr, p.energies, p.eta, slots=int(cols.size), iters=256)   # cached
             G2 = torch.empty_like(G0)
             rs.rsfd_shifted_cocg(h2.ptr, cols, p.energies, p.eta, p.tol, p.maxit, G2)
             Gh.copy_(G2, non_blocking=True)
@@ -345,7 +353,8 @@ def run_gpu(args):
                    "precision": p.precision, "boundary_rows": nb, "slots": slots_used,
                    "l2": "inputs larger than L2 (Krylov vectors of all slots: "
                          f"{3 * vsz * N * slots_used / 1e6:.0f} MB > 126 MB)",
-                   "parallelism": f"columns over {world} GPU(s), no collective"},
+                   "parallelism": f"columns over {world} GPU(s), no collective",
+                   "launch_options": tuned if tuned else "defaults"},
         "status": [int(x) for x in statuses], "mean_iterations_per_column": statistics.mean(iters),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -579,6 +588,55 @@ def run_tc_gemm(args):
                           "complex_tflops": fl / ms / 1e9, "tf32_tflops_issued": 3 * fl / ms / 1e9}), flush=True)
 
 
+def run_uneven_regions(args):
+    """The uneven batch of six transition regions (32x32x64 ... 72x72x112, 4th order, per-region energy
+    sets of 32-200 points and eta in {1e-3, 5e-4}), double-float: every region's launch options are
+    chosen by the autotuner (rsfd_autotune), then the first --ncols columns of each region are solved
+    (a) region after region and (b) all regions in one rsfd_shifted_cocg_regions call, whose regions
+    run concurrently.  One JSON line per form with columns x energies / s over the whole batch."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import make_problem
+    torch.cuda.set_device(0)
+    rs.load_library()
+    probs = make_problem("uneven_regions")
+    ncols = args.ncols or 8
+    prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[args.precision]
+    hs, outs, cols, tuned = [], [], [], []
+    for p in probs:
+        h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
+        c = p.cols[:ncols]
+        opts, us = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(c.size), iters=128)
+        tuned.append({"region": p.name, "grid": list(p.grid), "K": int(p.K), "eta": p.eta, "us_per_slot_iteration": us,
+                      "pass_kind": opts["pass_kind"], "tile_y": opts["tile_y"], "rows_per_thread": opts["rows_per_thread"],
+                      "z_chunk": opts["z_chunk"]})
+        hs.append(h)
+        cols.append(c)
+        outs.append(torch.zeros((p.K, c.size, h.nb), dtype=h.complex_dtype, device="cuda"))
+    units = float(sum(c.size * p.K for c, p in zip(cols, probs)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = []
+    for p, h, c, o in zip(probs, hs, cols, outs):
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, c, p.energies, p.eta, p.tol, p.maxit, o)
+        its.append(float(info["iters"].mean()))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    jobs = [dict(h=h.ptr, cols=c, energies=p.energies, eta=p.eta, tol=p.tol, maxit=p.maxit, G0_bb=o)
+            for p, h, c, o in zip(probs, hs, cols, outs)]
+    t0 = time.perf_counter()
+    st, per = rs.rsfd_shifted_cocg_regions(jobs)
+    torch.cuda.synchronize()
+    t_con = time.perf_counter() - t0
+    for form, t in (("region_after_region", t_seq), ("regions_in_one_call", t_con)):
+        print(json.dumps({"experiment": "uneven_regions", "form": form, "precision": args.precision,
+                          "columns_per_region": ncols, "seconds": t, "columns_x_energies": units,
+                          "value": units / t, "unit": UNIT, "mean_seed_iterations": its,
+                          "status": int(st), "tuned": tuned if form == "regions_in_one_call" else None}), flush=True)
+    for h in hs:
+        h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,10 +656,12 @@ def main():
     ap.add_argument("--iters-per-sync", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-option autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--experiment", default=None,
-                    choices=[None, "shift_scaling", "precision_speedup", "dyson_scaling", "tc_gemm"],
+                    choices=[None, "shift_scaling", "precision_speedup", "dyson_scaling", "tc_gemm",
+                             "uneven_regions"],
                     help="run an experiment instead of the benchmark (JSON lines)")
     ap.add_argument("--dyson-max-nb", type=int, default=0, help="dyson_scaling: largest boundary size (0 = all)")
     ap.add_argument("--gemm-size", type=int, default=0, help="tc_gemm: only the shapes with this m (0 = all)")
@@ -619,6 +679,9 @@ def main():
         return
     if args.experiment == "tc_gemm":
         run_tc_gemm(args)
+        return
+    if args.experiment == "uneven_regions":
+        run_uneven_regions(args)
         return
     if args.impl == "reference":
         run_reference(args)

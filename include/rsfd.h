@@ -208,6 +208,44 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
                               double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
                               void* G0_bb, rsfd_col_info* info, double* final_res);
 
+/* Launch-option autotuner for rsfd_shifted_cocg (the seed iteration and shift update of Sec. III B and
+ * the Appendix; the paper has no launch shapes, so the tuned quantities are this library's own):
+ * times short solves of `iters` seed iterations (at least two collapse lengths) of the handle's first
+ * `slots` boundary columns at the given energies for every candidate pass form, tile height, rows per
+ * thread and z-chunk, at the RHS block width `slots` and the handle's collapse length, and keeps the
+ * candidate with the least device time per (column, iteration).  The result is applied to the handle
+ * (rsfd_set_solve_options) and cached for the process by (grid, order, precision, projectors, K,
+ * slots); the Dyson options and the profile flag are kept.
+ *   energies host [K];  eta > 0;  slots >= 1 (at most the number of boundary rows is used);
+ *   best (nullable) receives the options;  us_per_slot_iteration (nullable) the measured time.
+ * The trial solves allocate their own output buffer.  RSFD_ERR_ARG on bad arguments,
+ * RSFD_ERR_ALLOC / RSFD_ERR_CUDA when no candidate could run. */
+rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
+                          rsfd_solve_opts* best, double* us_per_slot_iteration);
+
+/* One transition region's shifted-COCG solve (the arguments of rsfd_shifted_cocg) for
+ * rsfd_shifted_cocg_regions; status is written by the call. */
+typedef struct {
+  rsfd_handle h;
+  const int64_t* cols;
+  int32_t ncols;
+  const double* energies;
+  int32_t K;
+  double eta, tol;
+  int32_t maxit, seed_kind, seed_index;
+  void* G0_bb;
+  rsfd_col_info* info;
+  double* final_res;
+  rsfd_status status;
+} rsfd_region_solve;
+
+/* Shifted COCG (Sec. III B; Appendix) for several transition regions of different sizes in one call:
+ * every job runs rsfd_shifted_cocg on its own handle and stream, driven by its own host thread, so the
+ * regions' kernels overlap on the device.  Each handle may appear in one job only.  Returns the worst
+ * job status (an error before RSFD_ERR_BREAKDOWN before RSFD_ERR_NOT_CONVERGED before RSFD_OK);
+ * rsfd_last_error(NULL) names the failing region.  Results equal n separate calls. */
+rsfd_status rsfd_shifted_cocg_regions(int32_t n, rsfd_region_solve* jobs);
+
 /* Counters and timings of the last rsfd_shifted_cocg call on this handle. */
 rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out);
 

@@ -62,6 +62,15 @@ class rsfd_solve_opts(ctypes.Structure):
                 ("dyson_kind", ctypes.c_int32), ("dyson_refine", ctypes.c_int32)]
 
 
+class rsfd_region_solve(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("cols", ctypes.POINTER(ctypes.c_int64)), ("ncols", ctypes.c_int32),
+                ("energies", ctypes.POINTER(ctypes.c_double)), ("K", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("seed_kind", ctypes.c_int32),
+                ("seed_index", ctypes.c_int32), ("G0_bb", ctypes.c_void_p),
+                ("info", ctypes.POINTER(rsfd_col_info)), ("final_res", ctypes.POINTER(ctypes.c_double)),
+                ("status", ctypes.c_int)]
+
+
 class rsfd_stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_pass", ctypes.c_double), ("ms_shift", ctypes.c_double),
                 ("n_pass", ctypes.c_int64), ("n_shift", ctypes.c_int64), ("n_other", ctypes.c_int64),
@@ -85,6 +94,10 @@ _SIGNATURES = {
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                          ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
+    "rsfd_shifted_cocg_regions": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(rsfd_region_solve)]),
+    "rsfd_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(rsfd_solve_opts),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "rsfd_dyson_boundary": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_dyson_tracked": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_double)]),
     "rsfd_cgemm_tf32x3": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -250,6 +263,47 @@ def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_
                    dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
                           ("final_seed", np.int32)])
     return st, arr, res
+
+
+def rsfd_shifted_cocg_regions(jobs):
+    """Several regions in one call.  jobs: list of dicts with keys h (handle pointer), cols, energies,
+    eta, tol, maxit, G0_bb (device tensor) and optionally seed_kind, seed_index.  Returns
+    (worst status, [(status, info, final_res) per job])."""
+    import torch
+    lib = load_library()
+    n = len(jobs)
+    arr = (rsfd_region_solve * n)()
+    keep = []
+    for i, j in enumerate(jobs):
+        c, cp = _i64(j["cols"])
+        e, ep = _f64(j["energies"])
+        info = (rsfd_col_info * c.size)()
+        res = np.zeros((c.size, e.size), np.float64)
+        ptr = _dev_ptr(j["G0_bb"], (torch.complex64, torch.complex128), name="G0_bb")
+        keep.append((c, e, info, res))
+        arr[i] = rsfd_region_solve(j["h"], cp, int(c.size), ep, int(e.size), float(j["eta"]), float(j["tol"]),
+                                   int(j["maxit"]), int(j.get("seed_kind", RSFD_SEED_MID)), int(j.get("seed_index", 0)),
+                                   ptr, info, res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    st = lib.rsfd_shifted_cocg_regions(n, arr)
+    _check(None, st, allow=(RSFD_ERR_NOT_CONVERGED, RSFD_ERR_BREAKDOWN))
+    out = []
+    for i, (c, e, info, res) in enumerate(keep):
+        inf = np.array([(x.iters, x.switches, x.status, x.final_seed) for x in info],
+                       dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
+                              ("final_seed", np.int32)])
+        out.append((int(arr[i].status), inf, res))
+    return st, out
+
+
+def rsfd_autotune(h, energies, eta, slots, iters=128):
+    """Tune the handle's launch options on short solves; returns (options dict, us per slot-iteration)."""
+    lib = load_library()
+    e, ep = _f64(energies)
+    o = rsfd_solve_opts()
+    us = ctypes.c_double(0.0)
+    _check(h, lib.rsfd_autotune(h, ep, int(e.size), float(eta), int(slots), int(iters), ctypes.byref(o),
+                                ctypes.byref(us)))
+    return {k: getattr(o, k) for k, _ in rsfd_solve_opts._fields_}, float(us.value)
 
 
 def rsfd_get_stats(h) -> dict:

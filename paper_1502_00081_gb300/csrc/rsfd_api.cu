@@ -14,6 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -925,4 +928,161 @@ void rsfd_destroy(rsfd_handle h) {
   delete h;
 }
 
+
+// Launch-option autotuner: short solves (iters seed iterations, profile events on) of the handle's
+// first boundary columns at the caller's energies for every candidate (pass form, tile height, rows
+// per thread, z-chunk), keeping the least device time per slot-iteration.  Results are cached per
+// process by (grid, order, precision, projectors, K, slots).
+struct TuneKey {
+  int nx, ny, nz, fd, prec, proj, K, slots;
+  bool operator<(const TuneKey& o) const {
+    const int a[8] = {nx, ny, nz, fd, prec, proj, K, slots};
+    const int b[8] = {o.nx, o.ny, o.nz, o.fd, o.prec, o.proj, o.K, o.slots};
+    return std::lexicographical_compare(a, a + 8, b, b + 8);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<rsfd_solve_opts, double>> g_tune_cache;
+
+rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
+                          rsfd_solve_opts* best, double* us_per_slot_iteration) {
+  if (!h || !energies || K < 1 || !(eta > 0) || slots < 1 || iters < 1)
+    return fail(h, RSFD_ERR_ARG, "rsfd_autotune: bad argument");
+  const int ncols = std::min<long long>(slots, (long long)h->brow.size());
+  const TuneKey key{h->nx, h->ny, h->nz, h->fd_order, h->prec, h->n_atoms > 0 ? 1 : 0, (int)K, ncols};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      rsfd_solve_opts o = it->second.first;
+      o.profile = h->opts.profile;
+      o.dyson_kind = h->opts.dyson_kind;
+      o.dyson_refine = h->opts.dyson_refine;
+      h->opts = o;
+      if (best) *best = o;
+      if (us_per_slot_iteration) *us_per_slot_iteration = it->second.second;
+      return RSFD_OK;
+    }
+  }
+  const rsfd_solve_opts keep = h->opts;
+  const int C = keep.iters_per_sync > 0 ? keep.iters_per_sync : 32;
+  const int maxit = std::max<int>(iters, 2 * C);
+  std::vector<int64_t> cols(h->brow.begin(), h->brow.begin() + ncols);
+  void* G0 = nullptr;
+  const size_t gbytes = (size_t)K * ncols * h->nr * (h->prec == RSFD_MIXED ? 8 : 16);
+  if (cudaMalloc(&G0, gbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RSFD_ERR_ALLOC, "rsfd_autotune: cudaMalloc of the trial output failed");
+  }
+  std::vector<rsfd_col_info> info(ncols);
+  std::vector<double> res((size_t)ncols * K);
+  std::vector<rsfd_solve_opts> cand;
+  const int kinds[2] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE};
+  const int zcs[3] = {0, h->nz, (h->nz + 1) / 2};
+  for (int kind : kinds) {
+    if (kind == RSFD_PASS_RECOMPUTE && h->n_atoms > 0) continue;
+    const int rows_c[2] = {1, 2};
+    for (int rows : rows_c) {
+      if (kind == RSFD_PASS_RECOMPUTE && rows != 1) continue;
+      const int tys[3] = {0, 8, 16};
+      for (int ty : tys) {
+        if (kind == RSFD_PASS_RECOMPUTE && ty != 0) continue;
+        const int tyv = ty > 0 ? ty : default_tile_y(h->prec, h->R, h->ny, kind, rows);
+        if (ty > 0 && (ty == default_tile_y(h->prec, h->R, h->ny, kind, rows) || !tile_ok(h->prec, h->R, tyv, kind, rows)))
+          continue;
+        for (int zc : zcs) {
+          if (zc > 0 && zc < 8) continue;
+          rsfd_solve_opts o = keep;
+          o.pass_kind = kind;
+          o.rows_per_thread = kind == RSFD_PASS_STORED ? rows : 0;
+          o.tile_y = ty;
+          o.z_chunk = zc;
+          o.slots = ncols;
+          o.iters_per_sync = C;
+          o.profile = 1;
+          o.use_graphs = 0;
+          o.prefetch = 0;
+          cand.push_back(o);
+        }
+      }
+    }
+  }
+  double best_us = -1.0;
+  rsfd_solve_opts best_o = keep;
+  for (const rsfd_solve_opts& o : cand) {
+    if (rsfd_set_solve_options(h, &o) != RSFD_OK) continue;
+    const rsfd_status st = rsfd_shifted_cocg(h, cols.data(), ncols, energies, K, eta, 1e-30, maxit, RSFD_SEED_MID, 0,
+                                             G0, info.data(), res.data());
+    if (st != RSFD_OK && st != RSFD_ERR_NOT_CONVERGED) continue;
+    const double its = (double)h->stats.slot_iterations;
+    if (its <= 0) continue;
+    const double us = (h->stats.ms_pass + h->stats.ms_shift) * 1e3 / its;
+    if (best_us < 0 || us < best_us) {
+      best_us = us;
+      best_o = o;
+    }
+  }
+  cudaFree(G0);
+  if (best_us < 0) {
+    h->opts = keep;
+    return fail(h, RSFD_ERR_CUDA, "rsfd_autotune: no candidate ran");
+  }
+  best_o.profile = keep.profile;
+  best_o.use_graphs = keep.use_graphs;
+  best_o.prefetch = keep.prefetch;
+  h->opts = best_o;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(best_o, best_us);
+  }
+  if (best) *best = best_o;
+  if (us_per_slot_iteration) *us_per_slot_iteration = best_us;
+  return RSFD_OK;
+}
+
+
+// Several transition regions (each its own handle and stream) solved in one call: one host thread per
+// region drives that region's iteration chunks (CUDA graphs) on the handle's own stream, so the
+// regions' kernels run concurrently on the device and small regions fill the SMs that large ones
+// leave idle.  The worst status is returned; each job's own status is stored in the job.
+rsfd_status rsfd_shifted_cocg_regions(int32_t n, rsfd_region_solve* jobs) {
+  if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_regions: bad job list");
+  for (int i = 0; i < n; ++i) {
+    if (!jobs[i].h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_regions: NULL handle in job " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (jobs[j].h == jobs[i].h)
+        return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_regions: a handle appears in two jobs");
+  }
+  auto run = [](rsfd_region_solve* q) {
+    q->status = rsfd_shifted_cocg(q->h, q->cols, q->ncols, q->energies, q->K, q->eta, q->tol, q->maxit, q->seed_kind,
+                                  q->seed_index, q->G0_bb, q->info, q->final_res);
+  };
+  std::vector<std::thread> th;
+  th.reserve(n > 0 ? n - 1 : 0);
+  try {
+    for (int i = 1; i < n; ++i) th.emplace_back(run, &jobs[i]);
+  } catch (...) {
+    for (auto& t : th) t.join();
+    return fail(nullptr, RSFD_ERR_ALLOC, "rsfd_shifted_cocg_regions: could not start a host thread");
+  }
+  if (n > 0) run(&jobs[0]);
+  for (auto& t : th) t.join();
+  rsfd_status worst = RSFD_OK;
+  auto rank = [](rsfd_status st) {
+    if (st == RSFD_OK) return 0;
+    if (st == RSFD_ERR_NOT_CONVERGED) return 1;
+    if (st == RSFD_ERR_BREAKDOWN) return 2;
+    return 3;
+  };
+  for (int i = 0; i < n; ++i)
+    if (rank(jobs[i].status) > rank(worst)) worst = jobs[i].status;
+  if (rank(worst) == 3) {
+    for (int i = 0; i < n; ++i)
+      if (jobs[i].status == worst) {
+        g_last_error = "region " + std::to_string(i) + ": " + jobs[i].h->err;
+        break;
+      }
+  }
+  return worst;
+}
 }  // extern "C"
