@@ -32,10 +32,8 @@ constexpr int TC_THREADS = 128;
 constexpr int TC_PLANE_A = TC_BM * TC_KC * 4;   // bytes of one operand plane (8 KB)
 constexpr int TC_PLANE_B = TC_BN * TC_KC * 4;
 constexpr int TC_STAGE = 4 * TC_PLANE_A + 4 * TC_PLANE_B;
-constexpr int TC_NSTAGE = 2;
-// slack after the stages keeps every address the descriptors can form inside the allocation
-constexpr int TC_SLACK = 40 * 1024;
-constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + TC_SLACK + 1024;
+constexpr int TC_NSTAGE = 3;
+constexpr int TC_SMEM = TC_NSTAGE * TC_STAGE + 1024;
 constexpr int TC_TMEM_COLS = 2 * TC_BN;         // Re and Im accumulators
 // core-matrix strides of a plane: 8-row groups are adjacent (128 B apart, the "stride" offset
 // along M/N); groups of 4 K-elements are one plane-height apart (the "leading" offset along K)
@@ -115,7 +113,7 @@ __device__ __forceinline__ uint32_t plane_off(int row, int kgrp, int rows) {
 __global__ void __launch_bounds__(TC_THREADS, 1)
 cgemm_tf32x3_kernel(int m, int n, int k, float2 alpha, const float2* __restrict__ A, int lda, long long sA,
                     const float2* __restrict__ B, int ldb, long long sB, float beta, float2* C, int ldc,
-                    long long sC, int* err) {
+                    long long sC, int* err, int vecB) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   __shared__ __align__(8) uint64_t bars[TC_NSTAGE];
   __shared__ uint32_t tmem_base_s;
@@ -146,55 +144,70 @@ cgemm_tf32x3_kernel(int m, int n, int k, float2 alpha, const float2* __restrict_
 
   const int nchunks = (k + TC_KC - 1) / TC_KC;
   const uint32_t id_pos = idesc_tf32(TC_BM, TC_BN, 0), id_neg = idesc_tf32(TC_BM, TC_BN, 1);
-  bool ok = true;
-  for (int kc = 0; kc < nchunks && ok; ++kc) {
-    const int s = kc & 1;
-    unsigned char* st = smem + s * TC_STAGE;
-    if (kc >= 2) ok = bar_wait(smem_addr(&bars[s]), (uint32_t)(((kc - 2) >> 1) & 1));
+  // raw operands of one K-chunk, loaded into registers one chunk ahead of the shared-memory stores:
+  // thread tid holds row m0 + tid of A and column n0 + tid of B
+  float2 ra[TC_KC], rb[TC_KC];
+  auto load_chunk = [&](int kc) {
     const int k0 = kc * TC_KC;
-    // A: thread = row of the tile, 4 groups of 4 K-elements
-    {
-      const int i = tid, gi = m0 + i;
+    const int gi = m0 + tid, gj = n0 + tid;
 #pragma unroll
-      for (int g = 0; g < TC_KC / 4; ++g) {
-        float rh[4], rl[4], ih[4], il[4];
+    for (int q = 0; q < TC_KC; ++q) {
+      const int kk = k0 + q;
+      ra[q] = (gi < m && kk < k) ? A[(long long)kk * lda + gi] : make_float2(0.f, 0.f);
+    }
+    if (vecB && gj < n && k0 + TC_KC <= k) {
+      const float4* src = reinterpret_cast<const float4*>(B + (long long)gj * ldb + k0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int kk = k0 + 4 * g + q;
-          float2 v = make_float2(0.f, 0.f);
-          if (gi < m && kk < k) v = A[(long long)kk * lda + gi];
-          split3(v.x, rh[q], rl[q]);
-          split3(v.y, ih[q], il[q]);
-        }
-        const uint32_t o = plane_off(i, g, TC_BM);
-        *(float4*)(st + 0 * TC_PLANE_A + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-        *(float4*)(st + 1 * TC_PLANE_A + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-        *(float4*)(st + 2 * TC_PLANE_A + o) = make_float4(ih[0], ih[1], ih[2], ih[3]);
-        *(float4*)(st + 3 * TC_PLANE_A + o) = make_float4(il[0], il[1], il[2], il[3]);
+      for (int q = 0; q < TC_KC / 2; ++q) {
+        const float4 v = src[q];
+        rb[2 * q] = make_float2(v.x, v.y);
+        rb[2 * q + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < TC_KC; ++q) {
+        const int kk = k0 + q;
+        rb[q] = (gj < n && kk < k) ? B[(long long)gj * ldb + kk] : make_float2(0.f, 0.f);
       }
     }
-    // B: thread = column of the tile (a row of the K-major B operand)
-    {
-      const int j = tid, gj = n0 + j;
-      unsigned char* sb = st + 4 * TC_PLANE_A;
+  };
+  // split into TF32 hi / lo planes in the core-matrix layout of stage st
+  auto store_chunk = [&](unsigned char* st) {
+    unsigned char* sb = st + 4 * TC_PLANE_A;
 #pragma unroll
-      for (int g = 0; g < TC_KC / 4; ++g) {
-        float rh[4], rl[4], ih[4], il[4];
+    for (int g = 0; g < TC_KC / 4; ++g) {
+      float rh[4], rl[4], ih[4], il[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int kk = k0 + 4 * g + q;
-          float2 v = make_float2(0.f, 0.f);
-          if (gj < n && kk < k) v = B[(long long)gj * ldb + kk];
-          split3(v.x, rh[q], rl[q]);
-          split3(v.y, ih[q], il[q]);
-        }
-        const uint32_t o = plane_off(j, g, TC_BN);
-        *(float4*)(sb + 0 * TC_PLANE_B + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-        *(float4*)(sb + 1 * TC_PLANE_B + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-        *(float4*)(sb + 2 * TC_PLANE_B + o) = make_float4(ih[0], ih[1], ih[2], ih[3]);
-        *(float4*)(sb + 3 * TC_PLANE_B + o) = make_float4(il[0], il[1], il[2], il[3]);
+      for (int q = 0; q < 4; ++q) {
+        split3(ra[4 * g + q].x, rh[q], rl[q]);
+        split3(ra[4 * g + q].y, ih[q], il[q]);
       }
+      const uint32_t o = plane_off(tid, g, TC_BM);
+      *(float4*)(st + 0 * TC_PLANE_A + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+      *(float4*)(st + 1 * TC_PLANE_A + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+      *(float4*)(st + 2 * TC_PLANE_A + o) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+      *(float4*)(st + 3 * TC_PLANE_A + o) = make_float4(il[0], il[1], il[2], il[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split3(rb[4 * g + q].x, rh[q], rl[q]);
+        split3(rb[4 * g + q].y, ih[q], il[q]);
+      }
+      const uint32_t ob = plane_off(tid, g, TC_BN);
+      *(float4*)(sb + 0 * TC_PLANE_B + ob) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+      *(float4*)(sb + 1 * TC_PLANE_B + ob) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+      *(float4*)(sb + 2 * TC_PLANE_B + ob) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+      *(float4*)(sb + 3 * TC_PLANE_B + ob) = make_float4(il[0], il[1], il[2], il[3]);
     }
+  };
+  bool ok = true;
+  if (nchunks > 0) load_chunk(0);
+  for (int kc = 0; kc < nchunks && ok; ++kc) {
+    const int s = kc % TC_NSTAGE;
+    unsigned char* st = smem + s * TC_STAGE;
+    // the stage is free once the MMAs of chunk kc - TC_NSTAGE (its previous user) have completed
+    if (kc >= TC_NSTAGE) ok = bar_wait(smem_addr(&bars[s]), (uint32_t)(((kc - TC_NSTAGE) / TC_NSTAGE) & 1));
+    store_chunk(st);
+    if (kc + 1 < nchunks) load_chunk(kc + 1);   // in flight while this chunk's MMAs are issued
     // make the generic-proxy stores visible to the tensor core, then issue from one thread
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ok = __syncthreads_and(ok) != 0;   // uniform: a CTA whose wait expired stops as a whole
@@ -233,7 +246,8 @@ cgemm_tf32x3_kernel(int m, int n, int k, float2 alpha, const float2* __restrict_
     }
   }
   // the last commit covers every MMA issued before it
-  if (ok && nchunks > 0) ok = bar_wait(smem_addr(&bars[(nchunks - 1) & 1]), (uint32_t)(((nchunks - 1) >> 1) & 1));
+  if (ok && nchunks > 0)
+    ok = bar_wait(smem_addr(&bars[(nchunks - 1) % TC_NSTAGE]), (uint32_t)(((nchunks - 1) / TC_NSTAGE) & 1));
   ok = __syncthreads_and(ok) != 0;
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
@@ -474,8 +488,10 @@ cudaError_t cgemm_tf32x3(cudaStream_t st, int batch, int m, int n, int k, float2
     g_tc_attr_set[dev] = true;
   }
   dim3 grid((n + TC_BN - 1) / TC_BN, (m + TC_BM - 1) / TC_BM, batch);
+  // 16-byte loads of B columns when every column start (B + j ldb + k0, k0 a multiple of 16) is aligned
+  const int vecB = ((uintptr_t)B % 16 == 0) && (ldb % 2 == 0) && (sB % 2 == 0);
   cgemm_tf32x3_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
-                                                         err);
+                                                         err, vecB);
   return cudaGetLastError();
 }
 

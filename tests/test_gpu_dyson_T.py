@@ -162,7 +162,9 @@ def test_tracked_planes_interior_blocks(rs, prec, bound):
         SLo, SRo = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
         Gd = g_dense(p, Z, SLo, SRo, rows=trows, cols=trows)
         assert np.linalg.norm(Gm[k] - Gd) / np.linalg.norm(Gd) <= bound
-        assert np.linalg.norm(Gm[k][:nb, :nb] - Gbbm[k]) <= 1e-12 * np.linalg.norm(Gbbm[k])
+        # the same G_bb as rsfd_dyson_boundary, up to the refinement level of the two solves (the boundary
+        # step of a double-float handle is the tensor-core form with one FP64 refinement step)
+        assert np.linalg.norm(Gm[k][:nb, :nb] - Gbbm[k]) <= 1e-10 * np.linalg.norm(Gbbm[k])
         for e in range(len(planes)):
             blk = slice(nb + e * nxy, nb + (e + 1) * nxy)
             dos = -np.trace(Gm[k][blk, blk]).imag / np.pi

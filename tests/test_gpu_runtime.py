@@ -88,3 +88,34 @@ def test_regions_in_one_call_equal_separate_calls(rs):
     finally:
         for h in handles:
             h.close()
+
+
+def test_full_boundary_and_uneven_regions_full_size_first_iterations(rs):
+    """The full-boundary workload (48 x 48 x 160, 64 energies, eta 5e-4) and the six uneven regions
+    (32 x 32 x 64 ... 72 x 72 x 112, their own energy sets and eta) at full grid size, all seven in one
+    rsfd_shifted_cocg_regions call with their autotuned launch options: after 30 iterations the boundary
+    rows of x^(i) for two sampled columns per region equal the oracle's (double-float vectors)."""
+    from workloads import make_problem
+    probs = [make_problem("full_boundary")] + list(make_problem("uneven_regions"))
+    handles, outs, jobs, cols = [], [], [], []
+    try:
+        for p in probs:
+            h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_DF64)
+            c = p.cols[[0, len(p.cols) // 2 + 3]]
+            rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(c.size), iters=64)
+            o = torch.zeros((p.K, c.size, h.nb), dtype=torch.complex128, device="cuda")
+            handles.append(h)
+            outs.append(o)
+            cols.append(c)
+            jobs.append(dict(h=h.ptr, cols=c, energies=p.energies, eta=p.eta, tol=p.tol, maxit=30, G0_bb=o))
+        st, per = rs.rsfd_shifted_cocg_regions(jobs)
+        torch.cuda.synchronize()
+        assert st == rs.RSFD_ERR_NOT_CONVERGED
+        for (s, info, _), p, c, o in zip(per, probs, cols, outs):
+            assert s == rs.RSFD_ERR_NOT_CONVERGED and (info["iters"] == 30).all()
+            Go, res = shifted_cocg_columns(p, cols=c, maxit=30)
+            G = o.cpu().numpy().transpose(0, 2, 1)
+            assert relf(G, Go) <= 1e-6, p.name
+    finally:
+        for h in handles:
+            h.close()
