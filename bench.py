@@ -243,7 +243,8 @@ def run_gpu(args):
         # launch options picked by the library's autotuner for this block width (not timed)
         topts, tus = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(cols.size), iters=256)
         tuned = {"pass_kind": topts["pass_kind"], "tile_y": topts["tile_y"], "rows_per_thread": topts["rows_per_thread"],
-                 "z_chunk": topts["z_chunk"], "iters_per_sync": topts["iters_per_sync"], "us_per_slot_iteration": tus}
+                 "z_chunk": topts["z_chunk"], "iters_per_sync": topts["iters_per_sync"],
+                 "reg_budget": topts["reg_budget"], "us_per_slot_iteration": tus}
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
     stream = torch.cuda.current_stream()
 

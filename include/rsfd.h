@@ -134,6 +134,10 @@ typedef struct {
   int32_t dyson_kind;     /* rsfd_dyson_kind of rsfd_dyson_boundary */
   int32_t dyson_refine;   /* FP64 refinement steps of rsfd_dyson_boundary (0 = 2 for FP64 handles, 1 for
                              double-float and complex64 handles; at most 8) */
+  int32_t reg_budget;     /* RSFD_PASS_STORED, double-float, one row per thread: registers per thread of
+                             the pass, 0 = at most 96 (CTAs of <= 640 threads; two CTAs of <= 320 threads
+                             per SM), 1 = at most 128 (CTAs of <= 512 threads, tile_y <= 14, one CTA per
+                             SM, no register spills); other passes ignore it */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

@@ -1145,6 +1145,11 @@ constexpr int kFramePts = 3;        // frame points per frame thread
 // launch bound per rows-per-thread P (one point per thread needs the most threads)
 template <int P> struct MaxThreadsU { static constexpr int value = 384; };
 template <> struct MaxThreadsU<1> { static constexpr int value = 640; };
+// register-budget variants of the one-row-per-thread double-float pass: the launch bound caps the
+// registers a thread may use (65536 / bound), so a smaller bound trades CTAs per SM for fewer spills
+//   budget 0: bound 640 (96 registers; two CTAs of up to 320 threads per SM)
+//   budget 1: bound 512 (128 registers; one CTA per SM, tiles up to 14 rows)
+__host__ __device__ constexpr int passu_budget_threads(int budget) { return budget == 1 ? 512 : 640; }
 
 __host__ __device__ __forceinline__ int passu_frame_warps(int R, int tile_y) {
   const int nframe = 2 * R * tile_y + 2 * R * kTileX;
@@ -1172,8 +1177,8 @@ __device__ __forceinline__ void frame_point(int h, int TY, int nframe, int& cx, 
 template <typename VT> __device__ __forceinline__ VT zero_v() { return VT(); }
 template <> __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.f, 0.f); }
 
-template <int MODE, int R, int P>
-__global__ void __launch_bounds__(MaxThreadsU<P>::value) passu_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR) {
+template <int MODE, int R, int P, int NT = MaxThreadsU<P>::value>
+__global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR) {
   typedef Ops<MODE> O;
   typedef Stencil<MODE, R> ST;
   typedef typename O::C C;
@@ -1840,7 +1845,9 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   if (d.kind == RSFD_PASS_STORED) {
     const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth);
     const int thr = passu_threads(d.rows, R, d.tile_y);
-    if (d.rows == 1) passu_kernel<MODE, R, 1><<<grid, thr, smem, st>>>(p, *b.tmR);
+    if (d.rows == 1 && MODE == RSFD_DF64 && d.regs == 1)
+      passu_kernel<MODE, R, 1, passu_budget_threads(1)><<<grid, thr, smem, st>>>(p, *b.tmR);
+    else if (d.rows == 1) passu_kernel<MODE, R, 1><<<grid, thr, smem, st>>>(p, *b.tmR);
     else if (d.rows == 2) passu_kernel<MODE, R, 2><<<grid, thr, smem, st>>>(p, *b.tmR);
     else passu_kernel<MODE, R, 4><<<grid, thr, smem, st>>>(p, *b.tmR);
   } else {
@@ -1870,8 +1877,9 @@ int passu_box_off() { return kUBoxOff; }
 int passu_threads(int rows, int R, int tile_y) {
   return 32 * (tile_y / rows) + 32 * passu_frame_warps(R, tile_y);
 }
-int passu_max_threads(int rows) {
-  return rows == 1 ? MaxThreadsU<1>::value : rows == 2 ? MaxThreadsU<2>::value : MaxThreadsU<4>::value;
+int passu_max_threads(int rows, int budget) {
+  if (rows == 1) return passu_budget_threads(budget);
+  return rows == 2 ? MaxThreadsU<2>::value : MaxThreadsU<4>::value;
 }
 size_t passu_smem(int prec, int R, int tile_y, int depth) {
   const size_t es = prec == RSFD_MIXED ? 8 : 16;
@@ -1900,6 +1908,13 @@ cudaError_t kernels_init() {
   RSFD_ATTR(RSFD_DF64, 1)
   RSFD_ATTR(RSFD_DF64, 2)
 #undef RSFD_ATTR
+#define RSFD_ATTR_B(R, B)                                                                                \
+  if (e == cudaSuccess)                                                                                 \
+    e = cudaFuncSetAttribute(passu_kernel<RSFD_DF64, R, 1, passu_budget_threads(B)>,                    \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  RSFD_ATTR_B(1, 1)
+  RSFD_ATTR_B(2, 1)
+#undef RSFD_ATTR_B
   return e;
 }
 

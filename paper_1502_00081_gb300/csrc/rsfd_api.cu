@@ -238,11 +238,12 @@ static int resolve_rows(int opt) {
   return 1;
 }
 
-static bool tile_ok(int prec, int R, int tile_y, int kind, int rows) {
+static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget = 0) {
   if (tile_y < 1) return false;
   if (kind == RSFD_PASS_STORED) {
     if (tile_y % rows != 0) return false;
-    if (passu_threads(rows, R, tile_y) > passu_max_threads(rows)) return false;
+    const int b = (prec == RSFD_DF64 && rows == 1) ? budget : 0;
+    if (passu_threads(rows, R, tile_y) > passu_max_threads(rows, b)) return false;
   } else {
     if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
   }
@@ -511,6 +512,11 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
   if (o->prefetch > pass_max_depth())
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch must be <= " + std::to_string(pass_max_depth()));
   const int kind = resolve_kind(h->prec, o->pass_kind);
+  if (o->reg_budget < 0 || o->reg_budget > 1)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: reg_budget must be 0 or 1");
+  if (!tile_ok(h->prec, h->R, o->tile_y > 0 ? o->tile_y : default_tile_y(h->prec, h->R, h->ny, kind, rows), kind, rows,
+               o->reg_budget))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the tile does not fit the register budget's thread count");
   if (o->tile_y > 0 && !tile_ok(h->prec, h->R, o->tile_y, kind, rows))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: tile_y not allowed for this precision, stencil order and pass");
   if (o->prefetch > 0 && kind_smem(h->prec, h->R,
@@ -579,7 +585,9 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.nvec = d.kind == RSFD_PASS_STORED ? 5 : 3;
   d.rows = resolve_rows(h->opts.rows_per_thread);
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
-  if (!tile_ok(prec, h->R, d.tile_y, d.kind, d.rows)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
+  d.regs = (prec == RSFD_DF64 && d.rows == 1 && d.kind == RSFD_PASS_STORED) ? h->opts.reg_budget : 0;
+  if (!tile_ok(prec, h->R, d.tile_y, d.kind, d.rows, d.regs))
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
   // TMA prefetch depth: the option, else the deepest that fits in shared memory (fused pass: a CTA
   // alone on its SM) or 3 (stored-product pass: bundles are three times larger)
   if (h->opts.prefetch > 0) {
@@ -984,25 +992,29 @@ rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, doub
     const int rows_c[2] = {1, 2};
     for (int rows : rows_c) {
       if (kind == RSFD_PASS_RECOMPUTE && rows != 1) continue;
-      const int tys[3] = {0, 8, 16};
+      const int tys[4] = {0, 8, 12, 16};
       for (int ty : tys) {
         if (kind == RSFD_PASS_RECOMPUTE && ty != 0) continue;
         const int tyv = ty > 0 ? ty : default_tile_y(h->prec, h->R, h->ny, kind, rows);
-        if (ty > 0 && (ty == default_tile_y(h->prec, h->R, h->ny, kind, rows) || !tile_ok(h->prec, h->R, tyv, kind, rows)))
-          continue;
-        for (int zc : zcs) {
-          if (zc > 0 && zc < 8) continue;
-          rsfd_solve_opts o = keep;
-          o.pass_kind = kind;
-          o.rows_per_thread = kind == RSFD_PASS_STORED ? rows : 0;
-          o.tile_y = ty;
-          o.z_chunk = zc;
-          o.slots = ncols;
-          o.iters_per_sync = C;
-          o.profile = 1;
-          o.use_graphs = 0;
-          o.prefetch = 0;
-          cand.push_back(o);
+        if (ty > 0 && (ty == default_tile_y(h->prec, h->R, h->ny, kind, rows) || tyv > h->ny)) continue;
+        const int nb_budget = (h->prec == RSFD_DF64 && kind == RSFD_PASS_STORED && rows == 1) ? 2 : 1;
+        for (int budget = 0; budget < nb_budget; ++budget) {
+          if (!tile_ok(h->prec, h->R, tyv, kind, rows, budget)) continue;
+          for (int zc : zcs) {
+            if (zc > 0 && zc < 8) continue;
+            rsfd_solve_opts o = keep;
+            o.pass_kind = kind;
+            o.rows_per_thread = kind == RSFD_PASS_STORED ? rows : 0;
+            o.tile_y = ty;
+            o.z_chunk = zc;
+            o.reg_budget = budget;
+            o.slots = ncols;
+            o.iters_per_sync = C;
+            o.profile = 1;
+            o.use_graphs = 0;
+            o.prefetch = 0;
+            cand.push_back(o);
+          }
         }
       }
     }

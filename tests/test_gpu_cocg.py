@@ -197,3 +197,21 @@ def test_stored_pass_rows_per_thread(rs, rows, tile_y):
     assert st == rs.RSFD_OK
     Go, _ = shifted_cocg_columns(p)
     assert relf(G, Go) <= 1e-9
+
+
+@pytest.mark.parametrize("tile_y", [8, 12, 14])
+def test_double_float_register_budget_variant_identical(rs, tile_y):
+    """The 128-register variant of the one-row double-float stored pass (one CTA per SM, no spills)
+    computes exactly what the 96-register variant computes (same arithmetic, bit for bit), on ragged
+    tiles in x, y and z with seed switching."""
+    p = small_problem(grid=(45, 30, 21), h=0.45, fd_order=4, n_wells=4, n_energies=6, e_range=(0.3, 2.5),
+                      eta=4e-2, tol=1e-9, cols=4)
+    outs = []
+    for budget in (0, 1):
+        st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_DF64, opts=dict(pass_kind=2, rows_per_thread=1, tile_y=tile_y,
+                                                                      slots=3, z_chunk=9, reg_budget=budget))
+        assert st == rs.RSFD_OK
+        outs.append((G, info["iters"].copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    Go, _ = shifted_cocg_columns(p, tol=1e-11)
+    assert relf(outs[1][0], Go) <= 1e-6
