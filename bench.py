@@ -306,7 +306,9 @@ def run_gpu(args):
     if os.path.exists(tfile) and agg["n_pass"] > 0:
         try:
             t = json.load(open(tfile)).get(dom)
-            if t and t.get("workload") == p.name and t.get("precision") == p.precision:
+            lo = tuned or {"tile_y": args.tile_y, "z_chunk": args.z_chunk}
+            if (t and t.get("workload") == p.name and t.get("precision") == p.precision
+                    and t.get("tile_y") == lo.get("tile_y") and t.get("z_chunk") == lo.get("z_chunk")):
                 traffic = t["bytes_per_slot_iteration"] * agg["slot_iterations"] / agg["n_pass"]
         except Exception:
             traffic = None
