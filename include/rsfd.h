@@ -227,6 +227,22 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
 rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
                           rsfd_solve_opts* best, double* us_per_slot_iteration);
 
+/* Shifted COCG (Sec. III B; Appendix) over a long column list with checkpoints, so that a sweep that
+ * stops (a lost job, a reboot) resumes where it stopped.  The columns are solved in blocks of `block`
+ * with rsfd_shifted_cocg; after each block its slice of G0_bb and its rsfd_col_info entries are written
+ * to <dir>/g0_block_<b>.bin (b = block index, six digits; written under a temporary name, then
+ * renamed).  A block whose file exists and records the same inputs (operator: grid, h, order, faces,
+ * precision, V_loc, projectors; solve: the block's columns, energies, eta, tol, maxit, seed policy;
+ * checked by a 64-bit hash) is read back instead of solved.
+ *   dir      existing, writable directory (host string);  block >= 1.
+ *   G0_bb    device [K][ncols][nb] as in rsfd_shifted_cocg;  info host [ncols] (required).
+ *   blocks_resumed (nullable) receives the number of blocks read from their files.
+ * Status as rsfd_shifted_cocg (worst column outcome); RSFD_ERR_ARG when a file cannot be written. */
+rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                    int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                    int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
+                                    rsfd_col_info* info, int32_t* blocks_resumed);
+
 /* One transition region's shifted-COCG solve (the arguments of rsfd_shifted_cocg) for
  * rsfd_shifted_cocg_regions; status is written by the call. */
 typedef struct {

@@ -94,6 +94,11 @@ _SIGNATURES = {
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                          ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
+    "rsfd_shifted_cocg_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_char_p, _P, ctypes.POINTER(rsfd_col_info),
+                                               ctypes.POINTER(ctypes.c_int32)]),
     "rsfd_shifted_cocg_regions": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(rsfd_region_solve)]),
     "rsfd_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(rsfd_solve_opts),
@@ -264,6 +269,26 @@ def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_
                    dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
                           ("final_seed", np.int32)])
     return st, arr, res
+
+
+def rsfd_shifted_cocg_sweep(h, cols, energies, eta, tol, maxit, G0_bb, block, directory, seed_kind=RSFD_SEED_MID,
+                            seed_index=0):
+    """Checkpointed column sweep; returns (status, info structured array, blocks resumed from files)."""
+    import torch
+    lib = load_library()
+    c, cp = _i64(cols)
+    e, ep = _f64(energies)
+    ptr = _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
+    info = (rsfd_col_info * c.size)()
+    resumed = ctypes.c_int32(0)
+    st = lib.rsfd_shifted_cocg_sweep(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
+                                     int(seed_kind), int(seed_index), int(block), str(directory).encode(), ptr, info,
+                                     ctypes.byref(resumed))
+    _check(h, st, allow=(RSFD_ERR_NOT_CONVERGED, RSFD_ERR_BREAKDOWN))
+    arr = np.array([(i.iters, i.switches, i.status, i.final_seed) for i in info],
+                   dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
+                          ("final_seed", np.int32)])
+    return st, arr, int(resumed.value)
 
 
 def rsfd_shifted_cocg_regions(jobs):

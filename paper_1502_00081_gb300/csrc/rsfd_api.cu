@@ -54,6 +54,8 @@ struct Handle {
   long long *d_aidx = nullptr, *d_tpidx = nullptr;
   void *d_aval = nullptr, *d_tval = nullptr;
   double* d_aE = nullptr;
+  uint64_t in_hash = 0;        // hash of the operator's inputs (grid, h, order, faces, precision, V, projectors)
+  DevBuf sweep;                // one column block of G0_bb for rsfd_shifted_cocg_sweep
   rsfd_solve_opts opts;
   rsfd_stats stats;
   std::string err = "no error";
@@ -132,7 +134,7 @@ static void free_all(Handle* h) {
   DevBuf* bufs[] = {&h->rbuf,  &h->xbuf,      &h->pbuf,      &h->rhist,    &h->coef,
                     &h->eflag, &h->slots,     &h->shifts,    &h->partials, &h->tickets,
                     &h->Z,     &h->init_list, &h->init_grid, &h->counters, &h->pw,
-                    &h->pcorr, &h->pdots,     &h->ptickets};
+                    &h->pcorr, &h->pdots,     &h->ptickets,  &h->sweep};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -280,6 +282,16 @@ using namespace rsfd;
 
 struct rsfd_handle_s : public rsfd::Handle {};
 
+// FNV-1a, 64 bit: identifies the inputs a checkpointed column block was computed from
+static uint64_t fnv1a(uint64_t hv, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    hv ^= b[i];
+    hv *= 1099511628211ull;
+  }
+  return hv;
+}
+
 extern "C" {
 
 rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int32_t fd_order, int32_t n_face,
@@ -382,6 +394,21 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   }
   if (e == cudaSuccess) e = cudaMemcpy(h->dbrow, h->brow.data(), h->nb * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
+  {
+    uint64_t hv = 1469598103934665603ull;
+    const int32_t meta[6] = {grid[0], grid[1], grid[2], fd_order, n_face, precision};
+    hv = fnv1a(hv, meta, sizeof(meta));
+    hv = fnv1a(hv, &hh, sizeof(hh));
+    hv = fnv1a(hv, V_loc, (size_t)N * sizeof(double));
+    if (proj && proj->n_atoms > 0) {
+      const long long nnz = proj->ptr[proj->n_atoms];
+      hv = fnv1a(hv, proj->ptr, (size_t)(proj->n_atoms + 1) * sizeof(int64_t));
+      hv = fnv1a(hv, proj->idx, (size_t)nnz * sizeof(int64_t));
+      hv = fnv1a(hv, proj->val, (size_t)nnz * sizeof(double));
+      hv = fnv1a(hv, proj->E, (size_t)proj->n_atoms * sizeof(double));
+    }
+    h->in_hash = hv;
+  }
   if (proj && proj->n_atoms > 0) {
     // atom-major entries (padded vector indices, values in the potential's element type) and the
     // point-major transpose of the same entries (support points in ascending order, atoms ascending)
@@ -1094,6 +1121,93 @@ rsfd_status rsfd_shifted_cocg_regions(int32_t n, rsfd_region_solve* jobs) {
         g_last_error = "region " + std::to_string(i) + ": " + jobs[i].h->err;
         break;
       }
+  }
+  return worst;
+}
+
+// Column sweep with checkpoints: blocks of `block` columns are solved one after another; each
+// finished block's slice of G0_bb and its column outcomes go to <dir>/g0_block_<b>.bin (written to a
+// temporary name, then renamed), and a block whose file exists and was computed from the same inputs
+// is read back instead of solved.
+struct SweepHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t K, nb, ncols, elem_bytes, reserved;
+  uint64_t hash;
+};
+
+rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                    int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                    int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
+                                    rsfd_col_info* info, int32_t* blocks_resumed) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: NULL handle");
+  if (!cols || ncols < 1 || !energies || K < 1 || block < 1 || !dir || !dir[0] || !G0_bb || !info)
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: bad arguments");
+  const size_t es = h->prec == RSFD_MIXED ? 8 : 16;
+  const int nb = h->nr;
+  const int nblk = (ncols + block - 1) / block;
+  const int B0 = std::min(block, ncols);
+  rsfd_status s;
+  if ((s = ensure(h, h->sweep, (size_t)K * B0 * nb * es)) != RSFD_OK) return s;
+  if (blocks_resumed) *blocks_resumed = 0;
+  std::vector<unsigned char> host((size_t)K * B0 * nb * es);
+  rsfd_status worst = RSFD_OK;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int c0 = bi * block, B = std::min(block, ncols - c0);
+    uint64_t hv = h->in_hash;
+    hv = fnv1a(hv, cols + c0, (size_t)B * sizeof(int64_t));
+    hv = fnv1a(hv, energies, (size_t)K * sizeof(double));
+    const double dv[2] = {eta, tol};
+    const int32_t iv[5] = {maxit, seed_kind, seed_index, nb, (int32_t)es};
+    hv = fnv1a(hv, dv, sizeof(dv));
+    hv = fnv1a(hv, iv, sizeof(iv));
+    char name[64];
+    snprintf(name, sizeof(name), "/g0_block_%06d.bin", bi);
+    const std::string path = std::string(dir) + name;
+    const size_t bytes = (size_t)K * B * nb * es;
+    bool loaded = false;
+    if (FILE* f = fopen(path.c_str(), "rb")) {
+      SweepHeader hd;
+      if (fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "RSFDG0BK", 8) == 0 && hd.version == 1 &&
+          hd.K == K && hd.nb == nb && hd.ncols == B && hd.elem_bytes == (int32_t)es && hd.hash == hv &&
+          fread(info + c0, sizeof(rsfd_col_info), B, f) == (size_t)B && fread(host.data(), 1, bytes, f) == bytes)
+        loaded = true;
+      fclose(f);
+    }
+    if (loaded) {
+      RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, host.data(),
+                              (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyHostToDevice));
+      if (blocks_resumed) ++*blocks_resumed;
+    } else {
+      const rsfd_status st = rsfd_shifted_cocg(h, cols + c0, B, energies, K, eta, tol, maxit, seed_kind, seed_index,
+                                               h->sweep.p, info + c0, nullptr);
+      if (st != RSFD_OK && st != RSFD_ERR_NOT_CONVERGED && st != RSFD_ERR_BREAKDOWN) return st;
+      RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, h->sweep.p,
+                              (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyDeviceToDevice));
+      RSFD_CK(h, cudaMemcpy(host.data(), h->sweep.p, bytes, cudaMemcpyDeviceToHost));
+      SweepHeader hd;
+      memset(&hd, 0, sizeof(hd));
+      memcpy(hd.magic, "RSFDG0BK", 8);
+      hd.version = 1;
+      hd.K = K;
+      hd.nb = nb;
+      hd.ncols = B;
+      hd.elem_bytes = (int32_t)es;
+      hd.hash = hv;
+      const std::string tmp = path + ".tmp";
+      FILE* f = fopen(tmp.c_str(), "wb");
+      if (!f) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: cannot write " + tmp);
+      const bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                      fwrite(info + c0, sizeof(rsfd_col_info), B, f) == (size_t)B &&
+                      fwrite(host.data(), 1, bytes, f) == bytes;
+      if (fclose(f) != 0 || !ok || rename(tmp.c_str(), path.c_str()) != 0)
+        return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: cannot write " + path);
+    }
+    for (int c = c0; c < c0 + B; ++c) {
+      const rsfd_status cs = (rsfd_status)info[c].status;
+      if (cs == RSFD_ERR_BREAKDOWN) worst = RSFD_ERR_BREAKDOWN;
+      else if (cs == RSFD_ERR_NOT_CONVERGED && worst == RSFD_OK) worst = RSFD_ERR_NOT_CONVERGED;
+    }
   }
   return worst;
 }

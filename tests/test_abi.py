@@ -67,3 +67,15 @@ def test_host_lead_sigma_matches_oracle(lib, order, nx, ny):
         # ABI layout is column-major: array [k, c, a] = Sigma(a, c)
         assert np.abs(SR[k].T - SRo).max() < 1e-10 * max(1.0, np.abs(SRo).max())
         assert np.abs(SL[k].T - SLo).max() < 1e-10 * max(1.0, np.abs(SLo).max())
+
+
+def test_sweep_rejects_bad_arguments_without_gpu(lib):
+    rs, _ = lib
+    L = rs.load_library()
+    import ctypes
+    cols = (ctypes.c_int64 * 2)(0, 1)
+    en = (ctypes.c_double * 1)(0.5)
+    info = (rs.binding.rsfd_col_info * 2)()
+    # NULL handle, then a NULL directory: both rejected before any device work
+    assert L.rsfd_shifted_cocg_sweep(None, cols, 2, en, 1, 1e-2, 1e-8, 10, 0, 0, 1, b"/tmp", 1, info, None) == 1
+    assert L.rsfd_shifted_cocg_regions(-1, None) == 1
