@@ -1,4 +1,4 @@
-"""Self-energies of uniform V=0 finite-difference leads (oracle; test infrastructure).
+"""Self-energies of finite-difference leads (oracle; test infrastructure).
 
 Eqs. self-energy and surface green's function define Sigma_L = B^dag g_L B and
 Sigma_R = B g_R B^dag from the surface Green's function of a semi-infinite
@@ -80,8 +80,13 @@ def sigma_bloch(nx, ny, h, fd_order, Z):
     return SL, SR
 
 
-def _layer_blocks(nx, ny, h, fd_order):
-    """Principal-layer blocks of the lead (R planes per layer): H00, H01 (layer j -> j+1)."""
+def _layer_blocks(nx, ny, h, fd_order, V_layer=None):
+    """Principal-layer blocks of the lead (R planes per layer): H00, H01 (layer j -> j+1).
+
+    ``V_layer`` (optional, [R, Ny, Nx]) is the local potential of one principal layer, repeated in
+    every layer of the lead (a lead periodic along z with period R planes); it adds to H00's
+    diagonal.  None means V = 0.
+    """
     d = z_hoppings(h, fd_order)
     R = len(d) - 1
     nxy = nx * ny
@@ -92,8 +97,9 @@ def _layer_blocks(nx, ny, h, fd_order):
         return d[k] if k <= R else 0.0
     H00 = np.zeros((R * nxy, R * nxy))
     H01 = np.zeros((R * nxy, R * nxy))
+    V = np.zeros((R, nxy)) if V_layer is None else np.asarray(V_layer, dtype=np.float64).reshape(R, nxy)
     for a in range(R):
-        H00[a * nxy:(a + 1) * nxy, a * nxy:(a + 1) * nxy] = T2 + d[0] * np.eye(nxy)
+        H00[a * nxy:(a + 1) * nxy, a * nxy:(a + 1) * nxy] = T2 + d[0] * np.eye(nxy) + np.diag(V[a])
         for c in range(R):
             if c != a:
                 H00[a * nxy:(a + 1) * nxy, c * nxy:(c + 1) * nxy] = zc(abs(a - c)) * np.eye(nxy)
@@ -127,14 +133,20 @@ def surface_gf_sancho_rubio(H00, H01, Z, tol=1e-15, maxit=10000):
     return np.linalg.inv(Z * I - eps_s)
 
 
-def sigma_sancho_rubio(nx, ny, h, fd_order, Z):
-    """(Sigma_L, Sigma_R) from decimated surface Green's functions (Eq. self-energy)."""
-    H00, H01 = _layer_blocks(nx, ny, h, fd_order)
-    g = surface_gf_sancho_rubio(H00, H01, Z)
+def sigma_sancho_rubio(nx, ny, h, fd_order, Z, V_left=None, V_right=None):
+    """(Sigma_L, Sigma_R) from decimated surface Green's functions (Eq. self-energy).
+
+    ``V_left`` / ``V_right`` ([R, Ny, Nx] or None) are the potentials of one principal layer of each
+    lead, planes in increasing z; each lead repeats its layer (reading: a lead periodic along z whose
+    period is the coupling range R, the smallest principal layer of the stencil).
+    """
+    H00R, H01 = _layer_blocks(nx, ny, h, fd_order, V_right)
+    H00L, _ = _layer_blocks(nx, ny, h, fd_order, V_left)
+    g = surface_gf_sancho_rubio(H00R, H01, Z)
     # right lead: slab (last R planes) couples to the lead's first layer through H01
     SR = H01 @ g @ H01.T
     # left lead: chain running to -z; its layer couplings are H01^T and the slab couples through H01^T
-    gL = surface_gf_sancho_rubio(H00, H01.T, Z)
+    gL = surface_gf_sancho_rubio(H00L, H01.T, Z)
     SL = H01.T @ gL @ H01
     return SL, SR
 

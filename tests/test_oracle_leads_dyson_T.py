@@ -135,3 +135,48 @@ def test_planted_sigma_mistake_is_caught():
     G = g_dense(p, Z, SL, SR_bad, rows=b, cols=b)
     T, _ = transmission(G, SL, SR_bad)
     assert abs(T - 1.0) > 1e-2
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_sancho_rubio_constant_lead_potential_is_an_energy_shift(order):
+    """A constant lead potential v0 shifts the lead's spectrum: Sigma(Z; V = v0) = Sigma(Z - v0; V = 0),
+    and at V = 0 the decimation equals the Bloch-root closed form."""
+    nx, ny, h, Z, v0 = 4, 3, 0.5, 1.3 + 2e-2j, 0.37
+    R = order // 2
+    SL0, SR0 = sigma_sancho_rubio(nx, ny, h, order, Z - v0)
+    SLv, SRv = sigma_sancho_rubio(nx, ny, h, order, Z, V_left=np.full((R, ny, nx), v0),
+                                  V_right=np.full((R, ny, nx), v0))
+    assert np.abs(SLv - SL0).max() <= 1e-11 * np.abs(SL0).max()
+    assert np.abs(SRv - SR0).max() <= 1e-11 * np.abs(SR0).max()
+    SLb, SRb = sigma_bloch(nx, ny, h, order, Z - v0)
+    assert np.abs(SR0 - SRb).max() <= 1e-9 * np.abs(SRb).max()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_sancho_rubio_periodic_lead_fixed_point(order):
+    """A lead with a random layer potential: the decimated surface Green's function satisfies its own
+    defining relation g = (Z - H00 - H01 g H01^T)^{-1} (right lead) and the left lead's mirror form, and
+    Sigma is complex symmetric with a negative semidefinite anti-Hermitian part (retarded)."""
+    from oracle.leads import surface_gf_sancho_rubio
+    rng = np.random.Generator(np.random.PCG64(5))
+    nx, ny, h, Z = 4, 3, 0.5, 0.9 + 1e-2j
+    R = order // 2
+    VL = rng.uniform(-0.6, 0.2, size=(R, ny, nx))
+    VR = rng.uniform(-0.6, 0.2, size=(R, ny, nx))
+    H00R, H01 = _layer_blocks(nx, ny, h, order, VR)
+    H00L, _ = _layer_blocks(nx, ny, h, order, VL)
+    n = H00R.shape[0]
+    g = surface_gf_sancho_rubio(H00R, H01, Z)
+    res = np.linalg.inv(g) - (Z * np.eye(n) - H00R - H01 @ g @ H01.T)
+    assert np.abs(res).max() <= 1e-9 * np.abs(np.linalg.inv(g)).max()
+    gL = surface_gf_sancho_rubio(H00L, H01.T, Z)
+    resL = np.linalg.inv(gL) - (Z * np.eye(n) - H00L - H01.T @ gL @ H01)
+    assert np.abs(resL).max() <= 1e-9 * np.abs(np.linalg.inv(gL)).max()
+    SL, SR = sigma_sancho_rubio(nx, ny, h, order, Z, V_left=VL, V_right=VR)
+    for S in (SL, SR):
+        assert np.abs(S - S.T).max() <= 1e-12 * np.abs(S).max()
+        assert np.linalg.eigvalsh(0.5j * (S - S.conj().T)).min() >= -1e-12
+    # the lead potential changes Sigma (the layer potential enters the decimation)
+    SL0, SR0 = sigma_sancho_rubio(nx, ny, h, order, Z)
+    assert np.abs(SR - SR0).max() > 1e-2 * np.abs(SR0).max()
+    assert np.abs(SL - SL0).max() > 1e-2 * np.abs(SL0).max()
