@@ -327,6 +327,22 @@ rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma
 rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double h, int32_t fd_order, const double* energies,
                                     double eta, int32_t K, double* Sigma_L, double* Sigma_R);
 
+/* Self-energies of leads that repeat one principal layer of R = fd_order/2 planes with its own local
+ * potential (Eq. self-energy: Sigma_L = B^dag g_L B, Sigma_R = B g_R B^dag, with the surface Green's
+ * function of Eq. surface green's function of each semi-infinite lead), computed on the GPU in FP64 by
+ * the Lopez Sancho-Rubio decimation, batched over energies.  The leads continue the handle's grid (same
+ * Nx, Ny, h, order and Dirichlet walls); the handle's boundary slab must have R planes per side.
+ *   V_left, V_right  host [R][Ny][Nx] (nullable = 0): one principal layer of each lead, planes in
+ *                    increasing z, x fastest.
+ *   energies host [K];  eta > 0 (Z = E + i eta);  maxit >= 1 decimation steps (each doubles the
+ *   decimated length; about log2 of (lead decay length / layer) are needed, e.g. 20-40 at eta = 1e-3).
+ *   Sigma_L, Sigma_R device outputs [K][ns][ns] c128, ns = R Nx Ny, as rsfd_dyson_boundary takes them.
+ *   iterations (nullable) receives the largest number of steps used.
+ * RSFD_ERR_NOT_CONVERGED after maxit steps, RSFD_ERR_BREAKDOWN for a singular Z - eps. */
+rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, const double* V_right,
+                                       const double* energies, int32_t K, double eta, int32_t maxit, void* Sigma_L,
+                                       void* Sigma_R, int32_t* iterations);
+
 /* Size of the file-scope device array that rsfd_dyson_boundary_noalloc uses as scratch. */
 #define RSFD_NOALLOC_SCRATCH_BYTES (32u << 20)
 

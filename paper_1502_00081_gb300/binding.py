@@ -94,6 +94,9 @@ _SIGNATURES = {
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                          ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
+    "rsfd_lead_sigma_decimation": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                                  ctypes.c_int32, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "rsfd_shifted_cocg_sweep": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -269,6 +272,31 @@ def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_
                    dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
                           ("final_seed", np.int32)])
     return st, arr, res
+
+
+def rsfd_lead_sigma_decimation(h, energies, eta, V_left=None, V_right=None, maxit=200, ns=None):
+    """Lead self-energies by decimation on the GPU; returns (Sigma_L, Sigma_R) as complex128 CUDA
+    tensors [K, ns, ns] and the number of decimation steps used."""
+    import torch
+    lib = load_library()
+    e, ep = _f64(energies)
+    if ns is None:
+        ns = int(rsfd_boundary_rows(h).size) // 2
+    SL = torch.empty((e.size, ns, ns), dtype=torch.complex128, device="cuda")
+    SR = torch.empty_like(SL)
+    keep = []
+    ptrs = []
+    for V in (V_left, V_right):
+        if V is None:
+            ptrs.append(None)
+        else:
+            v, vp = _f64(np.asarray(V, dtype=np.float64).ravel())
+            keep.append(v)
+            ptrs.append(vp)
+    it = ctypes.c_int32(0)
+    _check(h, lib.rsfd_lead_sigma_decimation(h, ptrs[0], ptrs[1], ep, int(e.size), float(eta), int(maxit),
+                                             SL.data_ptr(), SR.data_ptr(), ctypes.byref(it)))
+    return SL, SR, int(it.value)
 
 
 def rsfd_shifted_cocg_sweep(h, cols, energies, eta, tol, maxit, G0_bb, block, directory, seed_kind=RSFD_SEED_MID,

@@ -15,6 +15,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cmath>
+#include <cstdlib>
+
 #include <string>
 #include <vector>
 
@@ -604,6 +607,208 @@ rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL,
   for (int k = 0; k < K; ++k)
     if (hinfo[k] != 0)
       return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_dyson_tracked: singular I - G0 Sigma at energy " + std::to_string(k));
+  return RSFD_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Lead self-energies by decimation (Eq. self-energy with the surface Green's function of Eq. surface
+// green's function), for leads that repeat one principal layer of R planes with its own potential.
+// Principal-layer blocks: H00 (in-plane kinetic + z couplings inside the layer + V), H01 (layer j to
+// j+1).  The right lead runs to +z (alpha_0 = H01, beta_0 = H01^T), the left lead to -z (alpha_0 =
+// H01^T, beta_0 = H01).  Lopez Sancho-Rubio iteration, batched over energies, all in FP64:
+//   g = (Z - eps)^{-1};  eps_s += alpha g beta;  eps += alpha g beta + beta g alpha;
+//   alpha = alpha g alpha;  beta = beta g beta;
+// until max |alpha|, |beta| fall below 1e-15 max |H01| for every energy; then g_s = (Z - eps_s)^{-1} and
+// Sigma_R = H01 g_s H01^T, Sigma_L = H01^T g_s H01.
+// ------------------------------------------------------------------------------------------------
+__global__ void zi_minus(double2* A, const double2* E, const double2* Z, int n, int batch) {
+  const long long n2 = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2 * batch;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n2, e = t - b * n2;
+    const long long c = e / n, r = e - c * n;
+    const double2 v = E[t];
+    A[t] = r == c ? make_double2(Z[b].x - v.x, Z[b].y - v.y) : make_double2(-v.x, -v.y);
+  }
+}
+// out[b] = max |re| + |im| over n2 entries of X[b] and of Y[b]
+__global__ void maxabs2_batched(const double2* X, const double2* Y, long long n2, double* out) {
+  const int b = blockIdx.x;
+  double m = 0.0;
+  for (long long i = threadIdx.x; i < n2; i += blockDim.x) {
+    const double2 x = X[(long long)b * n2 + i], y = Y[(long long)b * n2 + i];
+    m = fmax(m, fmax(fabs(x.x) + fabs(x.y), fabs(y.x) + fabs(y.y)));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = red[0];
+}
+// dst[b] = src (one n x n matrix broadcast to the batch)
+__global__ void bcast_c128(const double2* src, double2* dst, long long n2, int batch) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2 * batch;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[t % n2];
+}
+// rhs[b] = [X[b] | Y[b]]  (n x 2n, column-major)
+__global__ void concat_cols(const double2* X, const double2* Y, double2* rhs, long long n2, int batch) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * n2 * batch;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / (2 * n2), e = t - b * 2 * n2;
+    rhs[t] = e < n2 ? X[b * n2 + e] : Y[b * n2 + e - n2];
+  }
+}
+
+static void layer_blocks(int nx, int ny, double hh, int fd_order, const double* V, std::vector<double2>& H00,
+                         std::vector<double2>& H01) {
+  const int R = fd_order / 2, nxy = nx * ny, n = R * nxy;
+  const double c2[2] = {-2.0, 1.0}, c4[3] = {-2.5, 4.0 / 3.0, -1.0 / 12.0};
+  const double* c = fd_order == 2 ? c2 : c4;
+  double d[3] = {0, 0, 0};
+  for (int k = 0; k <= R; ++k) d[k] = -0.5 * c[k] / (hh * hh);
+  H00.assign((size_t)n * n, make_double2(0, 0));
+  H01.assign((size_t)n * n, make_double2(0, 0));
+  auto at = [&](std::vector<double2>& M, int r, int col) -> double2& { return M[(size_t)col * n + r]; };
+  for (int a = 0; a < R; ++a)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int i = a * nxy + y * nx + x;
+        at(H00, i, i).x += 3.0 * d[0] + (V ? V[i] : 0.0);   // x, y, z diagonal parts and the potential
+        for (int k = 1; k <= R; ++k) {
+          if (x + k < nx) { at(H00, i, i + k).x += d[k]; at(H00, i + k, i).x += d[k]; }
+          if (y + k < ny) { at(H00, i, i + k * nx).x += d[k]; at(H00, i + k * nx, i).x += d[k]; }
+        }
+        for (int cpl = 0; cpl < R; ++cpl) {
+          const int j = cpl * nxy + y * nx + x;
+          if (cpl != a && std::abs(a - cpl) <= R) at(H00, i, j).x += d[std::abs(a - cpl)];
+          const int dist = R + cpl - a;   // plane a of layer j to plane cpl of layer j + 1
+          if (dist <= R) at(H01, i, j).x += d[dist];
+        }
+      }
+}
+
+rsfd_status lead_decimation_run(Handle* h, const double* VL, const double* VR, const double* E, int K, double eta,
+                                int maxit, void* SLo, void* SRo, int* iters_out) {
+  const int nxy = handle_nx(h) * handle_ny(h);
+  const int R = handle_fd_order(h) / 2, n = R * nxy;
+  const long long n2 = (long long)n * n;
+  std::vector<double2> H00L, H00R, H01;
+  layer_blocks(handle_nx(h), handle_ny(h), handle_h(h), handle_fd_order(h), VL, H00L, H01);
+  layer_blocks(handle_nx(h), handle_ny(h), handle_h(h), handle_fd_order(h), VR, H00R, H01);
+  double hmax = 0.0;
+  for (const double2& v : H01) hmax = fmax(hmax, fabs(v.x));
+  const double tol = 1e-15 * fmax(1.0, hmax);
+  std::vector<double2> H01T((size_t)n2);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) H01T[(size_t)c * n + r] = H01[(size_t)r * n + c];
+  // per energy: eps_s, eps, alpha, beta, A (LU), Y (n x 2n), rhs (n x 2n), 2 products
+  const long long per = n2 * 11 * (long long)sizeof(double2) + (n + 64) * (long long)sizeof(int) + 64;
+  size_t free_b = 0, tot_b = 0;
+  DY_CK(h, cudaMemGetInfo(&free_b, &tot_b));
+  long long kc = (long long)(0.5 * (double)free_b) / per;
+  if (kc > K) kc = K;
+  if (kc < 1) kc = 1;
+  const int Kc = (int)kc;
+  rsfd_status s;
+  void *pW, *pC, *pPiv, *pZ;
+  if ((s = handle_ensure(h, 1, (size_t)n2 * 11 * Kc * sizeof(double2), &pW)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, (size_t)n2 * 3 * sizeof(double2), &pC)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 5, ((size_t)Kc * (n + 1) + 64) * sizeof(int), &pPiv)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 6, (size_t)Kc * (sizeof(double2) + sizeof(double)), &pZ)) != RSFD_OK) return s;
+  if ((s = handle_begin(h)) != RSFD_OK) return s;
+  cudaStream_t st = handle_stream(h);
+  double2* W = (double2*)pW;
+  double2 *eps_s = W, *eps = W + n2 * Kc, *al = W + 2 * n2 * Kc, *be = W + 3 * n2 * Kc, *A = W + 4 * n2 * Kc;
+  double2 *Y = W + 5 * n2 * Kc, *rhs = W + 7 * n2 * Kc, *P1 = W + 9 * n2 * Kc, *P2 = W + 10 * n2 * Kc;
+  double2 *dH00 = (double2*)pC, *dH01 = dH00 + n2, *dH01T = dH00 + 2 * n2;
+  int* piv = (int*)pPiv;
+  int* info = piv + (long long)Kc * n;
+  double2* dZ = (double2*)pZ;
+  double* dmax = (double*)(dZ + Kc);
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  DY_CK(h, cudaMemcpyAsync(dH01, H01.data(), n2 * sizeof(double2), cudaMemcpyHostToDevice, st));
+  DY_CK(h, cudaMemcpyAsync(dH01T, H01T.data(), n2 * sizeof(double2), cudaMemcpyHostToDevice, st));
+  int it_max = 0;
+  for (int lead = 0; lead < 2; ++lead) {
+    const std::vector<double2>& H00 = lead == 0 ? H00R : H00L;
+    double2* out = (double2*)(lead == 0 ? SRo : SLo);
+    const double2* a0 = lead == 0 ? dH01 : dH01T;
+    const double2* b0 = lead == 0 ? dH01T : dH01;
+    DY_CK(h, cudaMemcpyAsync(dH00, H00.data(), n2 * sizeof(double2), cudaMemcpyHostToDevice, st));
+    for (int k0 = 0; k0 < K; k0 += Kc) {
+      const int kb = K - k0 < Kc ? K - k0 : Kc;
+      const long long tot = n2 * kb;
+      std::vector<double2> Zh(kb);
+      for (int k = 0; k < kb; ++k) Zh[k] = make_double2(E[k0 + k], eta);
+      DY_CK(h, cudaMemcpyAsync(dZ, Zh.data(), kb * sizeof(double2), cudaMemcpyHostToDevice, st));
+      bcast_c128<<<grid_for(tot), 256, 0, st>>>(dH00, eps_s, n2, kb);
+      bcast_c128<<<grid_for(tot), 256, 0, st>>>(dH00, eps, n2, kb);
+      bcast_c128<<<grid_for(tot), 256, 0, st>>>(a0, al, n2, kb);
+      bcast_c128<<<grid_for(tot), 256, 0, st>>>(b0, be, n2, kb);
+      int it = 0;
+      for (; it < maxit; ++it) {
+        maxabs2_batched<<<kb, 256, 0, st>>>(al, be, n2, dmax);
+        std::vector<double> hm(kb);
+        DY_CK(h, cudaMemcpyAsync(hm.data(), dmax, kb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        DY_CK(h, cudaStreamSynchronize(st));
+        bool done = true;
+        for (int k = 0; k < kb; ++k) done &= hm[k] < tol;
+        if (done) break;
+        // g [alpha | beta] by LU of Z - eps
+        zi_minus<<<grid_for(tot), 256, 0, st>>>(A, eps, dZ, n, kb);
+        DY_CK(h, cudaMemsetAsync(info, 0, kb * sizeof(int), st));
+        getrf_blocked(st, A, n, kb, piv, info);
+        concat_cols<<<grid_for(2 * tot), 256, 0, st>>>(al, be, rhs, n2, kb);
+        copy_c128<<<grid_for(2 * tot), 256, 0, st>>>(rhs, Y, 2 * tot);
+        {
+          dim3 g((2 * n + 127) / 128, kb);
+          zgetrs_batched<<<g, 128, 0, st>>>(A, piv, Y, n, 2 * n);
+        }
+        const double2* ga = Y;        // g alpha, per energy stride 2 n2
+        const double2* gb = Y + n2;   // g beta
+        // P1 = alpha g beta, P2 = beta g alpha
+        zgemm(st, kb, n, n, n, one, al, n, n2, 0, gb, n, 2 * n2, zero, P1, n, n2);
+        zgemm(st, kb, n, n, n, one, be, n, n2, 0, ga, n, 2 * n2, zero, P2, n, n2);
+        axpy_c128<<<grid_for(tot), 256, 0, st>>>(eps_s, P1, tot);
+        axpy_c128<<<grid_for(tot), 256, 0, st>>>(eps, P1, tot);
+        axpy_c128<<<grid_for(tot), 256, 0, st>>>(eps, P2, tot);
+        // alpha <- alpha g alpha, beta <- beta g beta (through the product buffers)
+        zgemm(st, kb, n, n, n, one, al, n, n2, 0, ga, n, 2 * n2, zero, P1, n, n2);
+        zgemm(st, kb, n, n, n, one, be, n, n2, 0, gb, n, 2 * n2, zero, P2, n, n2);
+        copy_c128<<<grid_for(tot), 256, 0, st>>>(P1, al, tot);
+        copy_c128<<<grid_for(tot), 256, 0, st>>>(P2, be, tot);
+      }
+      it_max = it > it_max ? it : it_max;
+      // Sigma = b0 g_s a0 with g_s = (Z - eps_s)^{-1}:  X = g_s a0, Sigma = b0 X
+      //   right lead: b0 = H01, a0 = H01^T... the coupling into the lead and back out:
+      //   Sigma_R = H01 g_s H01^T, Sigma_L = H01^T g_s H01
+      zi_minus<<<grid_for(tot), 256, 0, st>>>(A, eps_s, dZ, n, kb);
+      DY_CK(h, cudaMemsetAsync(info, 0, kb * sizeof(int), st));
+      getrf_blocked(st, A, n, kb, piv, info);
+      bcast_c128<<<grid_for(tot), 256, 0, st>>>(lead == 0 ? dH01T : dH01, Y, n2, kb);
+      {
+        dim3 g((n + 127) / 128, kb);
+        zgetrs_batched<<<g, 128, 0, st>>>(A, piv, Y, n, n);
+      }
+      zgemm(st, kb, n, n, n, one, lead == 0 ? dH01 : dH01T, n, 0, 0, Y, n, n2, zero, out + n2 * k0, n, n2);
+      std::vector<int> hinfo(kb);
+      DY_CK(h, cudaMemcpyAsync(hinfo.data(), info, kb * sizeof(int), cudaMemcpyDeviceToHost, st));
+      DY_CK(h, cudaStreamSynchronize(st));
+      for (int k = 0; k < kb; ++k)
+        if (hinfo[k] != 0)
+          return handle_fail(h, RSFD_ERR_BREAKDOWN, "rsfd_lead_sigma_decimation: singular Z - eps at energy " +
+                                                        std::to_string(k0 + k));
+      if (it >= maxit)
+        return handle_fail(h, RSFD_ERR_NOT_CONVERGED, "rsfd_lead_sigma_decimation: no convergence in maxit steps");
+    }
+  }
+  DY_CK(h, cudaGetLastError());
+  if ((s = handle_end(h)) != RSFD_OK) return s;
+  if (iters_out) *iters_out = it_max;
   return RSFD_OK;
 }
 

@@ -106,6 +106,10 @@ rsfd_status handle_ensure(Handle* h, int idx, size_t bytes, void** out) {
 cudaStream_t handle_stream(Handle* h) { return h->work; }
 int handle_prec(Handle* h) { return h->prec; }
 int handle_nb(Handle* h) { return h->nb; }
+int handle_nx(Handle* h) { return h->nx; }
+int handle_ny(Handle* h) { return h->ny; }
+int handle_fd_order(Handle* h) { return h->fd_order; }
+double handle_h(Handle* h) { return h->h; }
 int handle_dyson_kind(Handle* h) {
   if (h->opts.dyson_kind != RSFD_DYSON_AUTO) return h->opts.dyson_kind;
   return h->prec == RSFD_FP64 ? RSFD_DYSON_FP64 : RSFD_DYSON_TC;
@@ -1210,5 +1214,24 @@ rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t 
     }
   }
   return worst;
+}
+
+rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, const double* V_right,
+                                       const double* energies, int32_t K, double eta, int32_t maxit, void* Sigma_L,
+                                       void* Sigma_R, int32_t* iterations) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_lead_sigma_decimation: NULL handle");
+  if (!energies || K < 1 || !(eta > 0) || maxit < 1 || !Sigma_L || !Sigma_R)
+    return fail(h, RSFD_ERR_ARG, "rsfd_lead_sigma_decimation: bad arguments");
+  if (h->nface != h->R)
+    return fail(h, RSFD_ERR_ARG, "rsfd_lead_sigma_decimation: the handle's boundary slab must have fd_order/2 planes");
+  const long long nl = (long long)h->R * h->nx * h->ny;
+  for (const double* V : {V_left, V_right})
+    if (V)
+      for (long long i = 0; i < nl; ++i)
+        if (!isfinite(V[i])) return fail(h, RSFD_ERR_ARG, "rsfd_lead_sigma_decimation: non-finite lead potential");
+  int it = 0;
+  rsfd_status s = lead_decimation_run(h, V_left, V_right, energies, K, eta, maxit, Sigma_L, Sigma_R, &it);
+  if (iterations) *iterations = it;
+  return s;
 }
 }  // extern "C"

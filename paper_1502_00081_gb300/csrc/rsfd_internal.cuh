@@ -205,6 +205,10 @@ rsfd_status handle_fail(Handle* h, rsfd_status s, const std::string& msg);
 rsfd_status handle_begin(Handle* h);
 rsfd_status handle_end(Handle* h);
 
+int handle_nx(Handle* h);
+int handle_ny(Handle* h);
+int handle_fd_order(Handle* h);
+double handle_h(Handle* h);
 int handle_dyson_kind(Handle* h);     // resolved: RSFD_DYSON_FP64 or RSFD_DYSON_TC
 int handle_dyson_refine(Handle* h);   // FP64 refinement steps of the Dyson solve
 
@@ -225,6 +229,8 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
 rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL, const void* SR, int K, void* G,
                               double* refres);
 rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const void* SR, int K, double* T);
+rsfd_status lead_decimation_run(Handle* h, const double* VL, const double* VR, const double* E, int K, double eta,
+                                int maxit, void* SL, void* SR, int* iters);
 
 // Host lead self-energy (lead_sigma.cpp).
 rsfd_status lead_sigma_uniform(int nx, int ny, double h, int fd_order, const double* E, double eta, int K,
