@@ -244,7 +244,7 @@ def run_gpu(args):
         topts, tus = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(cols.size), iters=256)
         tuned = {"pass_kind": topts["pass_kind"], "tile_y": topts["tile_y"], "rows_per_thread": topts["rows_per_thread"],
                  "z_chunk": topts["z_chunk"], "iters_per_sync": topts["iters_per_sync"],
-                 "reg_budget": topts["reg_budget"], "us_per_slot_iteration": tus}
+                 "reg_budget": topts["reg_budget"], "tile_x": topts["tile_x"], "us_per_slot_iteration": tus}
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
     stream = torch.cuda.current_stream()
 

@@ -138,6 +138,9 @@ typedef struct {
                              the pass, 0 = at most 96 (CTAs of <= 640 threads; two CTAs of <= 320 threads
                              per SM), 1 = at most 128 (CTAs of <= 512 threads, tile_y <= 14, one CTA per
                              SM, no register spills); other passes ignore it */
+  int32_t tile_x;         /* RSFD_PASS_STORED, double-float, one row per thread: tile width in x, 0 or 32
+                             (one tile row per warp) or 16 (two tile rows per warp; less idle work when Nx
+                             is an odd multiple of 16, e.g. 48 or 80); tile_y must be even */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

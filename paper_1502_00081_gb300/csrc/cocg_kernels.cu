@@ -1139,7 +1139,6 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
 // it in a shared-memory ring of R + 1 planes, and evaluates A r_n on plane q - R, whose x and y
 // neighbours were stored in earlier steps (rows inside the thread's own P come from registers).  One
 // barrier per plane.
-constexpr int kUBoxX = 36;
 constexpr int kUBoxOff = 2;
 constexpr int kFramePts = 3;        // frame points per frame thread
 // launch bound per rows-per-thread P (one point per thread needs the most threads)
@@ -1151,13 +1150,16 @@ template <> struct MaxThreadsU<1> { static constexpr int value = 640; };
 //   budget 1: bound 512 (128 registers; one CTA per SM, tiles up to 14 rows)
 __host__ __device__ constexpr int passu_budget_threads(int budget) { return budget == 1 ? 512 : 640; }
 
-__host__ __device__ __forceinline__ int passu_frame_warps(int R, int tile_y) {
-  const int nframe = 2 * R * tile_y + 2 * R * kTileX;
+// tile width TX in x: 32 (one tile row per warp) or 16 (two tile rows per warp, for grids whose Nx is
+// an odd multiple of 16); the box adds a 2-point frame on each side
+__host__ __device__ __forceinline__ int passu_frame_warps(int R, int tile_y, int TX = kTileX) {
+  const int nframe = 2 * R * tile_y + 2 * R * TX;
   return (nframe + 32 * kFramePts - 1) / (32 * kFramePts);
 }
+__host__ __device__ constexpr int passu_box_w(int TX) { return TX + 2 * kUBoxOff; }
 // box coordinates of frame point h (R columns left and right of every tile row, then R rows below
 // and above the tile); cx = -1 past the last one
-template <int R>
+template <int R, int TX = kTileX>
 __device__ __forceinline__ void frame_point(int h, int TY, int nframe, int& cx, int& cy) {
   cx = -1;
   cy = 0;
@@ -1165,19 +1167,19 @@ __device__ __forceinline__ void frame_point(int h, int TY, int nframe, int& cx, 
   if (h < 2 * R * TY) {
     const int side = h / (R * TY), k = h - side * R * TY;
     cy = k / R + R;
-    cx = side == 0 ? kUBoxOff - R + k % R : kUBoxOff + kTileX + k % R;
+    cx = side == 0 ? kUBoxOff - R + k % R : kUBoxOff + TX + k % R;
   } else {
     const int k2 = h - 2 * R * TY;
-    const int side = k2 / (R * kTileX), k = k2 - side * R * kTileX;
-    cx = kUBoxOff + k % kTileX;
-    cy = side == 0 ? k / kTileX : TY + R + k / kTileX;
+    const int side = k2 / (R * TX), k = k2 - side * R * TX;
+    cx = kUBoxOff + k % TX;
+    cy = side == 0 ? k / TX : TY + R + k / TX;
   }
 }
 
 template <typename VT> __device__ __forceinline__ VT zero_v() { return VT(); }
 template <> __device__ __forceinline__ float2 zero_v<float2>() { return make_float2(0.f, 0.f); }
 
-template <int MODE, int R, int P, int NT = MaxThreadsU<P>::value>
+template <int MODE, int R, int P, int NT = MaxThreadsU<P>::value, int TX = kTileX>
 __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR) {
   typedef Ops<MODE> O;
   typedef Stencil<MODE, R> ST;
@@ -1198,19 +1200,21 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
   const SolveDims& d = p.d;
   const int TY = d.tile_y;
   const int EY = TY + 2 * R;
-  constexpr int BW = kUBoxX;
+  constexpr int BW = passu_box_w(TX);
+  constexpr int HW = 32 / TX;                // tile rows per warp (1 or 2): lanes split into HW x-runs
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int xl = lane % TX;                  // x of the thread inside the tile
   const int cta = blockIdx.x;
   const int tz = cta % d.nzchunks;
   const int txy = cta / d.nzchunks;
   const int tx = txy % d.tiles_x, ty = txy / d.tiles_x;
   const int z0 = tz * d.zchunk;
   const int z1 = min(z0 + d.zchunk, d.nz);
-  const int x0 = tx * kTileX, y0 = ty * TY;
-  const int NWI = TY / P;
+  const int x0 = tx * TX, y0 = ty * TY;
+  const int NWI = TY / (P * HW);
   const bool interior = warp < NWI;
-  const int row0 = warp * P;                 // first tile row of a tile thread
-  const int gx = x0 + lane;
+  const int row0 = (warp * HW + lane / TX) * P;   // first tile row of a tile thread
+  const int gx = x0 + xl;
   const long long plane_elems = (long long)d.nxp * d.ny;
 
   // shared memory: per stage the boxes of r_{n-1}, r_{n-2}, u_{n-1}; a ring of R + 1 planes of r_n
@@ -1325,7 +1329,7 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
       C* sw = SB + (size_t)isw * PE;
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        const int o = (row0 + k + R) * BW + lane + kUBoxOff;
+        const int o = (row0 + k + R) * BW + xl + kUBoxOff;
         const size_t os = (size_t)ist * PE + o;
         const C rq = ST::combine(a1, RA[os], a2, RB[os], aA, UA[os]);   // Eq. rvec
         sw[o] = rq;
@@ -1354,7 +1358,7 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
       const C* P0 = SB + (size_t)((isw + 1 == R + 1) ? 0 : isw + 1) * PE;
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        const int o = (row0 + k + R) * BW + lane + kUBoxOff;
+        const int o = (row0 + k + R) * BW + xl + kUBoxOff;
         const C rc = zq[k][CC];
         C n1[6], n2[6];
         n1[0] = zq[k][(CC + Q - 1) % Q];
@@ -1397,14 +1401,14 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
       }
     }
   } else {
-    const int nframe = 2 * R * TY + 2 * R * kTileX;
-    const int FT = passu_frame_warps(R, TY) * 32;
+    const int nframe = 2 * R * TY + 2 * R * TX;
+    const int FT = passu_frame_warps(R, TY, TX) * 32;
     int fo[kFramePts];
     bool fv[kFramePts];
 #pragma unroll
     for (int j = 0; j < kFramePts; ++j) {
       int cx, cy;
-      frame_point<R>((warp - NWI) * 32 + lane + j * FT, TY, nframe, cx, cy);
+      frame_point<R, TX>((warp - NWI) * 32 + lane + j * FT, TY, nframe, cx, cy);
       fv[j] = cx >= 0;
       fo[j] = fv[j] ? cy * BW + cx : 0;
     }
@@ -1843,9 +1847,11 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.pdots = b.pdots;
   dim3 grid(d.ctas_per_slot, d.W);
   if (d.kind == RSFD_PASS_STORED) {
-    const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth);
-    const int thr = passu_threads(d.rows, R, d.tile_y);
-    if (d.rows == 1 && MODE == RSFD_DF64 && d.regs == 1)
+    const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth, d.tile_x);
+    const int thr = passu_threads(d.rows, R, d.tile_y, d.tile_x);
+    if (d.rows == 1 && MODE == RSFD_DF64 && d.tile_x == 16)
+      passu_kernel<MODE, R, 1, passu_budget_threads(0), 16><<<grid, thr, smem, st>>>(p, *b.tmR);
+    else if (d.rows == 1 && MODE == RSFD_DF64 && d.regs == 1)
       passu_kernel<MODE, R, 1, passu_budget_threads(1)><<<grid, thr, smem, st>>>(p, *b.tmR);
     else if (d.rows == 1) passu_kernel<MODE, R, 1><<<grid, thr, smem, st>>>(p, *b.tmR);
     else if (d.rows == 2) passu_kernel<MODE, R, 2><<<grid, thr, smem, st>>>(p, *b.tmR);
@@ -1871,19 +1877,19 @@ size_t pass_smem(int prec, int R, int tile_y, int depth) {
   return (size_t)(R + 1 + depth + stages + R + 2) * pc + stages * pv + 128;
 }
 int pass_max_depth() { return kMaxDepth; }
-int passu_box_x() { return kUBoxX; }
+int passu_box_x(int tile_x) { return passu_box_w(tile_x); }
 int passu_box_off() { return kUBoxOff; }
 // tile threads (one x column and P rows each) plus the frame warps
-int passu_threads(int rows, int R, int tile_y) {
-  return 32 * (tile_y / rows) + 32 * passu_frame_warps(R, tile_y);
+int passu_threads(int rows, int R, int tile_y, int tile_x) {
+  return 32 * (tile_y / rows) / (32 / tile_x) + 32 * passu_frame_warps(R, tile_y, tile_x);
 }
 int passu_max_threads(int rows, int budget) {
   if (rows == 1) return passu_budget_threads(budget);
   return rows == 2 ? MaxThreadsU<2>::value : MaxThreadsU<4>::value;
 }
-size_t passu_smem(int prec, int R, int tile_y, int depth) {
+size_t passu_smem(int prec, int R, int tile_y, int depth, int tile_x) {
   const size_t es = prec == RSFD_MIXED ? 8 : 16;
-  const size_t pb = ((size_t)kUBoxX * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
+  const size_t pb = ((size_t)passu_box_w(tile_x) * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
   const size_t stages = (size_t)depth + 1;
   return stages * 3 * pb + (size_t)(R + 1) * pb + 128;
 }
@@ -1915,6 +1921,12 @@ cudaError_t kernels_init() {
   RSFD_ATTR_B(1, 1)
   RSFD_ATTR_B(2, 1)
 #undef RSFD_ATTR_B
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(passu_kernel<RSFD_DF64, 1, 1, passu_budget_threads(0), 16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(passu_kernel<RSFD_DF64, 2, 1, passu_budget_threads(0), 16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return e;
 }
 

@@ -196,7 +196,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // is the true Nx, so reads past the last column (and outside the grid) come back as zeros.
 // Boxes: fused pass 40 x (tile_y + 4R) for both; stored-product pass 36 x (tile_y + 2R) for the
 // vectors and the 32 x tile_y tile for the potential.
-static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind) {
+static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const bool f64 = h->prec == RSFD_FP64;
@@ -206,8 +206,8 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind) {
   const bool stored = kind == RSFD_PASS_STORED;
   const cuuint64_t nvec = stored ? 5 : 3;
   const cuuint32_t EY = (cuuint32_t)(tile_y + (stored ? 2 : 4) * h->R);
-  const cuuint32_t BX = (cuuint32_t)(stored ? passu_box_x() : pass_box_x());
-  const cuuint32_t VBX = (cuuint32_t)(stored ? pass_tile_x(h->R) : pass_box_x());
+  const cuuint32_t BX = (cuuint32_t)(stored ? passu_box_x(tile_x) : pass_box_x());
+  const cuuint32_t VBX = (cuuint32_t)(stored ? tile_x : pass_box_x());
   const cuuint32_t VBY = stored ? (cuuint32_t)tile_y : EY;
   {
     cuuint64_t dims[4] = {mR * h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->nz, nvec * W};
@@ -235,8 +235,8 @@ static int resolve_kind(int, int opt) {
   return RSFD_PASS_STORED;
 }
 
-static size_t kind_smem(int prec, int R, int tile_y, int depth, int kind) {
-  return kind == RSFD_PASS_STORED ? passu_smem(prec, R, tile_y, depth) : pass_smem(prec, R, tile_y, depth);
+static size_t kind_smem(int prec, int R, int tile_y, int depth, int kind, int tile_x = 32) {
+  return kind == RSFD_PASS_STORED ? passu_smem(prec, R, tile_y, depth, tile_x) : pass_smem(prec, R, tile_y, depth);
 }
 
 static int resolve_rows(int opt) {
@@ -244,17 +244,22 @@ static int resolve_rows(int opt) {
   return 1;
 }
 
-static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget = 0) {
+static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget = 0, int tile_x = 32) {
   if (tile_y < 1) return false;
+  if (tile_x != 32) {
+    // the 16-wide tile: one-row double-float stored pass with the default register budget only
+    if (tile_x != 16 || kind != RSFD_PASS_STORED || prec != RSFD_DF64 || rows != 1 || budget != 0) return false;
+    if (tile_y % 2 != 0) return false;
+  }
   if (kind == RSFD_PASS_STORED) {
     if (tile_y % rows != 0) return false;
     const int b = (prec == RSFD_DF64 && rows == 1) ? budget : 0;
-    if (passu_threads(rows, R, tile_y) > passu_max_threads(rows, b)) return false;
+    if (passu_threads(rows, R, tile_y, tile_x) > passu_max_threads(rows, b)) return false;
   } else {
     if (pass_threads(R, tile_y) > pass_max_threads(prec)) return false;
   }
   if (tile_y + 4 * R > 256) return false;
-  return kind_smem(prec, R, tile_y, 1, kind) <= (size_t)(216 * 1024);
+  return kind_smem(prec, R, tile_y, 1, kind, tile_x) <= (size_t)(216 * 1024);
 }
 
 // Fused pass: the tile height that minimises the rows computed per column of tiles,
@@ -545,9 +550,13 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
   const int kind = resolve_kind(h->prec, o->pass_kind);
   if (o->reg_budget < 0 || o->reg_budget > 1)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: reg_budget must be 0 or 1");
+  if (o->tile_x != 0 && o->tile_x != 16 && o->tile_x != 32)
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: tile_x must be 0, 16 or 32");
+  const int txo = o->tile_x == 16 ? 16 : 32;
   if (!tile_ok(h->prec, h->R, o->tile_y > 0 ? o->tile_y : default_tile_y(h->prec, h->R, h->ny, kind, rows), kind, rows,
-               o->reg_budget))
-    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the tile does not fit the register budget's thread count");
+               o->reg_budget, txo))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the tile does not fit this pass, precision, register budget "
+                                 "or tile width");
   if (o->tile_y > 0 && !tile_ok(h->prec, h->R, o->tile_y, kind, rows))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: tile_y not allowed for this precision, stencil order and pass");
   if (o->prefetch > 0 && kind_smem(h->prec, h->R,
@@ -617,8 +626,9 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   d.rows = resolve_rows(h->opts.rows_per_thread);
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
   d.regs = (prec == RSFD_DF64 && d.rows == 1 && d.kind == RSFD_PASS_STORED) ? h->opts.reg_budget : 0;
-  if (!tile_ok(prec, h->R, d.tile_y, d.kind, d.rows, d.regs))
-    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y");
+  d.tile_x = (h->opts.tile_x == 16 && d.kind == RSFD_PASS_STORED) ? 16 : 32;
+  if (!tile_ok(prec, h->R, d.tile_y, d.kind, d.rows, d.regs, d.tile_x))
+    return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y / tile_x");
   // TMA prefetch depth: the option, else the deepest that fits in shared memory (fused pass: a CTA
   // alone on its SM) or 3 (stored-product pass: bundles are three times larger)
   if (h->opts.prefetch > 0) {
@@ -627,14 +637,17 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
     d.depth = 1;
     const int dmax = d.kind == RSFD_PASS_STORED ? 3 : pass_max_depth();
     for (int dp = dmax; dp >= 1; --dp)
-      if (kind_smem(prec, h->R, d.tile_y, dp, d.kind) <= (size_t)(216 * 1024)) {
+      if (kind_smem(prec, h->R, d.tile_y, dp, d.kind, d.tile_x) <= (size_t)(216 * 1024)) {
         d.depth = dp;
         break;
       }
   }
-  if (kind_smem(prec, h->R, d.tile_y, d.depth, d.kind) > (size_t)(216 * 1024))
+  if (kind_smem(prec, h->R, d.tile_y, d.depth, d.kind, d.tile_x) > (size_t)(216 * 1024))
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: prefetch depth does not fit in shared memory");
-  d.tiles_x = (h->nx + pass_tile_x(h->R) - 1) / pass_tile_x(h->R);
+  {
+    const int tw = d.kind == RSFD_PASS_STORED ? d.tile_x : pass_tile_x(h->R);
+    d.tiles_x = (h->nx + tw - 1) / tw;
+  }
   d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
   int W0 = h->opts.slots > 0 ? h->opts.slots : 256;
   W0 = std::min(W0, ncols);
@@ -685,7 +698,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   if ((s = ensure(h, h->init_list, (size_t)W * 2 * sizeof(int))) != RSFD_OK) return s;
   if ((s = ensure(h, h->init_grid, (size_t)W * sizeof(long long))) != RSFD_OK) return s;
   if ((s = ensure(h, h->counters, 4 * sizeof(unsigned long long))) != RSFD_OK) return s;
-  if ((s = make_maps(h, W, d.tile_y, d.kind)) != RSFD_OK) return s;
+  if ((s = make_maps(h, W, d.tile_y, d.kind, d.tile_x)) != RSFD_OK) return s;
   SolverBuffers b;
   memset(&b, 0, sizeof(b));
   b.rbuf = h->rbuf.p;
@@ -1028,9 +1041,13 @@ rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, doub
         if (kind == RSFD_PASS_RECOMPUTE && ty != 0) continue;
         const int tyv = ty > 0 ? ty : default_tile_y(h->prec, h->R, h->ny, kind, rows);
         if (ty > 0 && (ty == default_tile_y(h->prec, h->R, h->ny, kind, rows) || tyv > h->ny)) continue;
-        const int nb_budget = (h->prec == RSFD_DF64 && kind == RSFD_PASS_STORED && rows == 1) ? 2 : 1;
-        for (int budget = 0; budget < nb_budget; ++budget) {
-          if (!tile_ok(h->prec, h->R, tyv, kind, rows, budget)) continue;
+        const bool df1 = h->prec == RSFD_DF64 && kind == RSFD_PASS_STORED && rows == 1;
+        // (register budget, tile width): 96 or 128 registers at width 32, and the 16-wide tile
+        const int variants[3][2] = {{0, 32}, {1, 32}, {0, 16}};
+        for (int vi = 0; vi < (df1 ? 3 : 1); ++vi) {
+          const int budget = variants[vi][0], twx = variants[vi][1];
+          if (twx == 16 && h->nx % 32 == 0) continue;   // the 16-wide tile only helps ragged widths
+          if (!tile_ok(h->prec, h->R, tyv, kind, rows, budget, twx)) continue;
           for (int zc : zcs) {
             if (zc > 0 && zc < 8) continue;
             rsfd_solve_opts o = keep;
@@ -1039,6 +1056,7 @@ rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, doub
             o.tile_y = ty;
             o.z_chunk = zc;
             o.reg_budget = budget;
+            o.tile_x = twx == 16 ? 16 : 0;
             o.slots = ncols;
             o.iters_per_sync = C;
             o.profile = 1;

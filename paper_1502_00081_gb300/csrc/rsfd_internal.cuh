@@ -110,7 +110,8 @@ struct SolveDims {
   int kind;           // RSFD_PASS_RECOMPUTE or RSFD_PASS_STORED
   int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
   int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
-  int regs;           // register budget of the one-row double-float pass (0, 1, 2)
+  int regs;           // register budget of the one-row double-float pass (0, 1)
+  int tile_x;         // stored-product pass tile width in x: 32, or 16 (one-row double-float pass)
 };
 
 struct Handle;   // defined in rsfd_api.cu
@@ -182,10 +183,10 @@ size_t vec_elem_bytes(int prec);
 size_t pot_elem_bytes(int prec);
 size_t hist_elem_bytes(int prec);
 size_t pass_smem(int prec, int R, int tile_y, int depth);
-size_t passu_smem(int prec, int R, int tile_y, int depth);
-int passu_threads(int rows, int R, int tile_y);
+size_t passu_smem(int prec, int R, int tile_y, int depth, int tile_x);
+int passu_threads(int rows, int R, int tile_y, int tile_x);
 int passu_max_threads(int rows, int budget);
-int passu_box_x();
+int passu_box_x(int tile_x);
 int passu_box_off();
 int pass_max_depth();
 int pass_box_x();

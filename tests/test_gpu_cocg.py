@@ -215,3 +215,24 @@ def test_double_float_register_budget_variant_identical(rs, tile_y):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     Go, _ = shifted_cocg_columns(p, tol=1e-11)
     assert relf(outs[1][0], Go) <= 1e-6
+
+
+@pytest.mark.parametrize("grid,order,tile_y", [((48, 26, 19), 4, 8), ((40, 30, 17), 4, 14), ((48, 20, 15), 2, 16)])
+def test_double_float_sixteen_wide_tiles(rs, grid, order, tile_y):
+    """The 16-wide tile of the one-row double-float stored pass (two tile rows per warp), on grids whose
+    width is an odd multiple of 16 or ragged, against the oracle; the 32-wide tile (another summation
+    order of the dot products) agrees with it within the double-float error (~1e-7, the FP32 leading
+    parts of the recorded residual rows)."""
+    p = small_problem(grid=grid, h=0.45, fd_order=order, n_wells=4, n_energies=6, e_range=(0.3, 2.5),
+                      eta=4e-2, tol=1e-10, cols=4)
+    outs = []
+    for tx in (16, 32):
+        st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_DF64, opts=dict(pass_kind=2, rows_per_thread=1, tile_y=tile_y,
+                                                                      slots=3, z_chunk=7, tile_x=tx))
+        assert st == rs.RSFD_OK
+        outs.append((G, info["iters"].copy()))
+    Go, _ = shifted_cocg_columns(p, tol=1e-12)
+    assert relf(outs[0][0], Go) <= 1e-6
+    assert relf(outs[0][0], outs[1][0]) <= 1e-6
+    # near the double-float floor the iteration count follows the rounding of the dots (a few per cent)
+    assert (np.abs(outs[0][1] - outs[1][1]) <= 0.05 * outs[1][1]).all()
