@@ -441,7 +441,6 @@ struct AccDF {
     addprod(ra_s, ra_l, ny, nyl, make_float2(vh.y, vh.x), make_float2(vl.y, vl.x));
     nn = __fmaf_rn(rh.x, rh.x, __fmaf_rn(rh.y, rh.y, nn));
   }
-  __device__ __forceinline__ void add(float2 r, float2 v) { add2(r, make_float2(0.f, 0.f), v, make_float2(0.f, 0.f)); }
   __device__ __forceinline__ void add(const dfc& r, const dfc& v) { add2(r.h, r.l, v.h, v.l); }
   static __device__ __forceinline__ float2 shfl2(float2 v, int o) {
     return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
@@ -1148,7 +1147,7 @@ template <> struct MaxThreadsU<1> { static constexpr int value = 640; };
 // registers a thread may use (65536 / bound), so a smaller bound trades CTAs per SM for fewer spills
 //   budget 0: bound 640 (96 registers; two CTAs of up to 320 threads per SM)
 //   budget 1: bound 512 (128 registers; one CTA per SM, tiles up to 14 rows)
-__host__ __device__ constexpr int passu_budget_threads(int budget) { return budget == 1 ? 512 : 640; }
+__host__ __device__ constexpr int passu_budget_threads(int budget) { return budget == 1 ? 512 : MaxThreadsU<1>::value; }
 
 // tile width TX in x: 32 (one tile row per warp) or 16 (two tile rows per warp, for grids whose Nx is
 // an odd multiple of 16); the box adds a 2-point frame on each side

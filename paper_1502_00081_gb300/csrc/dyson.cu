@@ -379,7 +379,7 @@ rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* 
   if (kc < 1) kc = 1;
   const int Kc = (int)kc;
   rsfd_status s;
-  void *pM, *pX, *pR, *pF, *pXf, *pPiv, *pRed, *pG0;
+  void *pM, *pX, *pR, *pF, *pPiv, *pRed, *pG0;
   if ((s = handle_ensure(h, 1, n2 * Kc * sizeof(double2), &pM)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 3, n2 * Kc * sizeof(double2), &pX)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 4, n2 * Kc * sizeof(double2), &pR)) != RSFD_OK) return s;

@@ -119,3 +119,38 @@ def test_full_boundary_and_uneven_regions_full_size_first_iterations(rs):
     finally:
         for h in handles:
             h.close()
+
+
+def test_regions_report_a_failing_region(rs):
+    """A region whose arguments are invalid (tol outside (0, 1)) fails alone: its status is the error,
+    the other region still solves, and the call returns the error with the region named."""
+    p = small_problem(grid=(10, 9, 12), h=0.5, fd_order=2, n_wells=2, n_energies=3, e_range=(0.4, 1.6),
+                      eta=5e-2, tol=1e-10, cols=2, seed=8)
+    handles = [rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_FP64) for _ in range(2)]
+    try:
+        outs = [torch.zeros((p.K, p.cols.size, h.nb), dtype=torch.complex128, device="cuda") for h in handles]
+        jobs = [dict(h=handles[0].ptr, cols=p.cols, energies=p.energies, eta=p.eta, tol=p.tol, maxit=p.maxit,
+                     G0_bb=outs[0]),
+                dict(h=handles[1].ptr, cols=p.cols, energies=p.energies, eta=p.eta, tol=2.0, maxit=p.maxit,
+                     G0_bb=outs[1])]
+        with pytest.raises(rs.RsfdError) as e:
+            rs.rsfd_shifted_cocg_regions(jobs)
+        assert e.value.status == rs.RSFD_ERR_ARG
+        assert "region 1" in rs.rsfd_last_error(None)
+        torch.cuda.synchronize()
+        Go, _ = shifted_cocg_columns(p, tol=1e-12)
+        G = outs[0].cpu().numpy().transpose(0, 2, 1)
+        assert relf(G, Go) <= 1e-9
+    finally:
+        for h in handles:
+            h.close()
+
+
+def test_sweep_rejects_an_unwritable_directory(rs, tmp_path):
+    p = small_problem(grid=(8, 7, 10), h=0.5, fd_order=2, n_wells=1, n_energies=2, eta=5e-2, tol=1e-8, cols=2)
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_FP64) as h:
+        G = torch.zeros((p.K, p.cols.size, h.nb), dtype=torch.complex128, device="cuda")
+        with pytest.raises(rs.RsfdError) as e:
+            rs.rsfd_shifted_cocg_sweep(h.ptr, p.cols, p.energies, p.eta, p.tol, p.maxit, G, 1,
+                                       str(tmp_path / "missing" / "dir"))
+        assert e.value.status == rs.RSFD_ERR_ARG
