@@ -238,13 +238,25 @@ rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, doub
  * precision, V_loc, projectors; solve: the block's columns, energies, eta, tol, maxit, seed policy;
  * checked by a 64-bit hash) is read back instead of solved.
  *   dir      existing, writable directory (host string);  block >= 1.
- *   G0_bb    device [K][ncols][nb] as in rsfd_shifted_cocg;  info host [ncols] (required).
+ *   G0_bb    device [K][ncols][nb] as in rsfd_shifted_cocg, or NULL to keep the results in the files only
+ *            (read back by energy with rsfd_sweep_load_energies);  info host [ncols] (required).
  *   blocks_resumed (nullable) receives the number of blocks read from their files.
  * Status as rsfd_shifted_cocg (worst column outcome); RSFD_ERR_ARG when a file cannot be written. */
 rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
                                     int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
                                     rsfd_col_info* info, int32_t* blocks_resumed);
+
+/* Energies k0 .. k0 + kcount - 1 of a completed rsfd_shifted_cocg_sweep (same handle inputs and the
+ * same cols, energies, eta, tol, maxit, seed policy, block and dir), every column, read from its block
+ * files: G0_part device [kcount][ncols][nb], the layout of rsfd_shifted_cocg's G0_bb for those energies,
+ * ready for rsfd_dyson_boundary on that energy chunk (the energy-chunked G0_bb of Sec. III B's boundary
+ * blocks when all K energies do not fit in device memory).  RSFD_ERR_ARG when a block file is missing,
+ * short, or was computed from other inputs. */
+rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                     int32_t seed_index, int32_t block, const char* dir, int32_t k0, int32_t kcount,
+                                     void* G0_part);
 
 /* One transition region's shifted-COCG solve (the arguments of rsfd_shifted_cocg) for
  * rsfd_shifted_cocg_regions; status is written by the call. */

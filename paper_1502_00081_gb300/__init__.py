@@ -18,7 +18,7 @@ from .binding import (  # noqa: F401
     RSFD_PASS_AUTO, RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED, RSFD_DYSON_AUTO, RSFD_DYSON_FP64, RSFD_DYSON_TC,
     RsfdError, lib_path, load_library,
     rsfd_create, rsfd_boundary_rows, rsfd_set_tracked_planes, rsfd_tracked_rows, rsfd_dyson_tracked,
-    rsfd_set_solve_options, rsfd_shifted_cocg, rsfd_get_stats, rsfd_autotune, rsfd_shifted_cocg_regions, rsfd_shifted_cocg_sweep,
+    rsfd_set_solve_options, rsfd_shifted_cocg, rsfd_get_stats, rsfd_autotune, rsfd_shifted_cocg_regions, rsfd_shifted_cocg_sweep, rsfd_sweep_load_energies,
     rsfd_dyson_boundary, rsfd_dyson_boundary_noalloc, rsfd_cgemm_tf32x3, rsfd_transmission, rsfd_lead_sigma_uniform, rsfd_lead_sigma_decimation, rsfd_last_error, rsfd_destroy,
     Handle,
 )

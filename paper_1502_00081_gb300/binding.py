@@ -103,6 +103,10 @@ _SIGNATURES = {
                                                ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_char_p, _P, ctypes.POINTER(rsfd_col_info),
                                                ctypes.POINTER(ctypes.c_int32)]),
+    "rsfd_sweep_load_energies": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32, _P]),
     "rsfd_shifted_cocg_regions": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(rsfd_region_solve)]),
     "rsfd_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(rsfd_solve_opts),
@@ -308,7 +312,7 @@ def rsfd_shifted_cocg_sweep(h, cols, energies, eta, tol, maxit, G0_bb, block, di
     lib = load_library()
     c, cp = _i64(cols)
     e, ep = _f64(energies)
-    ptr = _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
+    ptr = None if G0_bb is None else _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
     info = (rsfd_col_info * c.size)()
     resumed = ctypes.c_int32(0)
     st = lib.rsfd_shifted_cocg_sweep(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
@@ -319,6 +323,19 @@ def rsfd_shifted_cocg_sweep(h, cols, energies, eta, tol, maxit, G0_bb, block, di
                    dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),
                           ("final_seed", np.int32)])
     return st, arr, int(resumed.value)
+
+
+def rsfd_sweep_load_energies(h, cols, energies, eta, tol, maxit, block, directory, k0, kcount, G0_part,
+                             seed_kind=RSFD_SEED_MID, seed_index=0):
+    """Energies k0 .. k0+kcount-1 of a completed checkpointed sweep into G0_part [kcount, ncols, nb]."""
+    import torch
+    lib = load_library()
+    c, cp = _i64(cols)
+    e, ep = _f64(energies)
+    ptr = _dev_ptr(G0_part, (torch.complex64, torch.complex128), name="G0_part")
+    _check(h, lib.rsfd_sweep_load_energies(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
+                                           int(seed_kind), int(seed_index), int(block), str(directory).encode(),
+                                           int(k0), int(kcount), ptr))
 
 
 def rsfd_shifted_cocg_regions(jobs):

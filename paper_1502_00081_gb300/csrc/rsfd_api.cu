@@ -1158,12 +1158,24 @@ struct SweepHeader {
   uint64_t hash;
 };
 
+static uint64_t sweep_block_hash(const Handle* h, const int64_t* cols, int B, const double* energies, int K, double eta,
+                                 double tol, int maxit, int seed_kind, int seed_index, int nb, size_t es) {
+  uint64_t hv = h->in_hash;
+  hv = fnv1a(hv, cols, (size_t)B * sizeof(int64_t));
+  hv = fnv1a(hv, energies, (size_t)K * sizeof(double));
+  const double dv[2] = {eta, tol};
+  const int32_t iv[5] = {maxit, seed_kind, seed_index, nb, (int32_t)es};
+  hv = fnv1a(hv, dv, sizeof(dv));
+  hv = fnv1a(hv, iv, sizeof(iv));
+  return hv;
+}
+
 rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
                                     int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
                                     rsfd_col_info* info, int32_t* blocks_resumed) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: NULL handle");
-  if (!cols || ncols < 1 || !energies || K < 1 || block < 1 || !dir || !dir[0] || !G0_bb || !info)
+  if (!cols || ncols < 1 || !energies || K < 1 || block < 1 || !dir || !dir[0] || !info)
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg_sweep: bad arguments");
   const size_t es = h->prec == RSFD_MIXED ? 8 : 16;
   const int nb = h->nr;
@@ -1176,13 +1188,7 @@ rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t 
   rsfd_status worst = RSFD_OK;
   for (int bi = 0; bi < nblk; ++bi) {
     const int c0 = bi * block, B = std::min(block, ncols - c0);
-    uint64_t hv = h->in_hash;
-    hv = fnv1a(hv, cols + c0, (size_t)B * sizeof(int64_t));
-    hv = fnv1a(hv, energies, (size_t)K * sizeof(double));
-    const double dv[2] = {eta, tol};
-    const int32_t iv[5] = {maxit, seed_kind, seed_index, nb, (int32_t)es};
-    hv = fnv1a(hv, dv, sizeof(dv));
-    hv = fnv1a(hv, iv, sizeof(iv));
+    const uint64_t hv = sweep_block_hash(h, cols + c0, B, energies, K, eta, tol, maxit, seed_kind, seed_index, nb, es);
     char name[64];
     snprintf(name, sizeof(name), "/g0_block_%06d.bin", bi);
     const std::string path = std::string(dir) + name;
@@ -1197,15 +1203,17 @@ rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t 
       fclose(f);
     }
     if (loaded) {
-      RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, host.data(),
-                              (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyHostToDevice));
+      if (G0_bb)
+        RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, host.data(),
+                                (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyHostToDevice));
       if (blocks_resumed) ++*blocks_resumed;
     } else {
       const rsfd_status st = rsfd_shifted_cocg(h, cols + c0, B, energies, K, eta, tol, maxit, seed_kind, seed_index,
                                                h->sweep.p, info + c0, nullptr);
       if (st != RSFD_OK && st != RSFD_ERR_NOT_CONVERGED && st != RSFD_ERR_BREAKDOWN) return st;
-      RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, h->sweep.p,
-                              (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyDeviceToDevice));
+      if (G0_bb)
+        RSFD_CK(h, cudaMemcpy2D((unsigned char*)G0_bb + (size_t)c0 * nb * es, (size_t)ncols * nb * es, h->sweep.p,
+                                (size_t)B * nb * es, (size_t)B * nb * es, K, cudaMemcpyDeviceToDevice));
       RSFD_CK(h, cudaMemcpy(host.data(), h->sweep.p, bytes, cudaMemcpyDeviceToHost));
       SweepHeader hd;
       memset(&hd, 0, sizeof(hd));
@@ -1251,5 +1259,50 @@ rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, cons
   rsfd_status s = lead_decimation_run(h, V_left, V_right, energies, K, eta, maxit, Sigma_L, Sigma_R, &it);
   if (iterations) *iterations = it;
   return s;
+}
+
+// Energies k0 .. k0 + kcount - 1 of a completed checkpointed sweep, all columns, read from the block
+// files into a device buffer [kcount][ncols][nb]: the energy-chunked G0_bb of a sweep whose whole
+// G0_bb does not fit in device memory.
+rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                     int32_t seed_index, int32_t block, const char* dir, int32_t k0, int32_t kcount,
+                                     void* G0_part) {
+  if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_sweep_load_energies: NULL handle");
+  if (!cols || ncols < 1 || !energies || K < 1 || block < 1 || !dir || !dir[0] || !G0_part || k0 < 0 || kcount < 1 ||
+      k0 + kcount > K)
+    return fail(h, RSFD_ERR_ARG, "rsfd_sweep_load_energies: bad arguments");
+  const size_t es = h->prec == RSFD_MIXED ? 8 : 16;
+  const int nb = h->nr;
+  const int nblk = (ncols + block - 1) / block;
+  std::vector<unsigned char> host((size_t)std::min(block, ncols) * nb * es);
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int c0 = bi * block, B = std::min(block, ncols - c0);
+    const uint64_t hv = sweep_block_hash(h, cols + c0, B, energies, K, eta, tol, maxit, seed_kind, seed_index, nb, es);
+    char name[64];
+    snprintf(name, sizeof(name), "/g0_block_%06d.bin", bi);
+    const std::string path = std::string(dir) + name;
+    FILE* f = fopen(path.c_str(), "rb");
+    if (!f) return fail(h, RSFD_ERR_ARG, "rsfd_sweep_load_energies: missing " + path);
+    SweepHeader hd;
+    const bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && memcmp(hd.magic, "RSFDG0BK", 8) == 0 && hd.version == 1 &&
+                    hd.K == K && hd.nb == nb && hd.ncols == B && hd.elem_bytes == (int32_t)es && hd.hash == hv;
+    if (!ok) {
+      fclose(f);
+      return fail(h, RSFD_ERR_ARG, "rsfd_sweep_load_energies: " + path + " was computed from other inputs");
+    }
+    const size_t slice = (size_t)B * nb * es;
+    const long base = (long)sizeof(SweepHeader) + (long)B * (long)sizeof(rsfd_col_info);
+    for (int k = k0; k < k0 + kcount; ++k) {
+      if (fseek(f, base + (long)k * (long)slice, SEEK_SET) != 0 || fread(host.data(), 1, slice, f) != slice) {
+        fclose(f);
+        return fail(h, RSFD_ERR_ARG, "rsfd_sweep_load_energies: short read of " + path);
+      }
+      RSFD_CK(h, cudaMemcpy((unsigned char*)G0_part + ((size_t)(k - k0) * ncols + c0) * nb * es, host.data(), slice,
+                            cudaMemcpyHostToDevice));
+    }
+    fclose(f);
+  }
+  return RSFD_OK;
 }
 }  // extern "C"
