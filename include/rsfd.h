@@ -11,7 +11,13 @@
  *   2. the perturbed boundary Green's function G_bb from G0_bb and the lead
  *      self-energies through the exact OBM/Dyson relation (Eq. sec3-01a,
  *      Eqs. sec3-02 ... sec3-06);
- *   3. the Fisher-Lee transmission T(E) (Eq. TF).
+ *   3. the Fisher-Lee transmission T(E) (Eq. TF);
+ *   4. the lead self-energies those steps take (Eqs. self-energy, surface green's function):
+ *      closed form for uniform leads on the host, decimation for leads with a layer potential
+ *      on the GPU.
+ * Around them: a launch-option autotuner, several regions in one call, checkpointed column
+ * sweeps with energy-chunked read-back, interior diagonal blocks (DOS), the Dyson step's
+ * tensor-core GEMM, and an allocation-free Dyson entry point.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
