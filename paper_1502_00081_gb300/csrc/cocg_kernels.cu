@@ -1628,6 +1628,8 @@ struct ChunkParams {
   void* pbuf;
   const SlotState* slots;
   const ShiftCoef* coef;
+  void* wbuf;                // [W][K][2][hist_len] H: W_x, W_p of the collapse
+  double2* ebuf;             // [W][K][2]: e_x, e_p
   unsigned long long* counters;
   int hist_len;
 };
@@ -1656,52 +1658,76 @@ template <> struct XUpd<RSFD_DF64> {
   }
 };
 
+// Collapse coefficients of every (slot, energy), one thread each: backward recurrences
+//   A_l = ca_l + cb_{l+1} A_{l+1},  B_l = cb_{l+1} B_{l+1}  (A_{hc-1} = ca_{hc-1}, B_{hc-1} = 1),
+//   W_x[l] = A_l cr_l, W_p[l] = B_l cr_l, e_x = cb_0 A_0, e_p = cb_0 B_0   (FP64, rounded to H for W).
 template <int MODE>
-__global__ void __launch_bounds__(256) chunk_kernel(ChunkParams p) {
+__global__ void __launch_bounds__(256) chunk_coef_kernel(ChunkParams p) {
+  typedef typename Ops<MODE>::HR HR;
+  typedef HOps<HR> HO;
+  typedef typename HO::H H;
+  const SolveDims& d = p.d;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.W * d.K) return;
+  const int slot = t / d.K, i = t - slot * d.K;
+  const int hc = p.slots[slot].hcnt;
+  if (hc <= 0) return;
+  const ShiftCoef* cf = p.coef + ((size_t)slot * d.K + i) * p.hist_len;
+  H* Wx = reinterpret_cast<H*>(p.wbuf) + ((size_t)slot * d.K + i) * 2 * p.hist_len;
+  H* Wp = Wx + p.hist_len;
+  double2 A = cf[hc - 1].ca, B = make_double2(1.0, 0.0);
+  Wx[hc - 1] = HO::from(cmul(A, cf[hc - 1].cr));
+  Wp[hc - 1] = HO::from(cmul(B, cf[hc - 1].cr));
+  for (int l = hc - 2; l >= 0; --l) {
+    A = cadd(cf[l].ca, cmul(cf[l + 1].cb, A));
+    B = cmul(cf[l + 1].cb, B);
+    Wx[l] = HO::from(cmul(A, cf[l].cr));
+    Wp[l] = HO::from(cmul(B, cf[l].cr));
+  }
+  p.ebuf[((size_t)slot * d.K + i) * 2] = cmul(cf[0].cb, A);
+  p.ebuf[((size_t)slot * d.K + i) * 2 + 1] = cmul(cf[0].cb, B);
+  atomicAdd(&p.counters[0], (unsigned long long)hc);
+  if (i == 0) atomicAdd(&p.counters[2], 1ull);
+}
+
+// Apply the collapsed update: a block owns kChunkRows boundary rows of one slot, stages those rows'
+// residual history once in shared memory (each thread its own row) and sweeps every energy,
+//   x <- x + e_x p + sum_l W_x[l] r_l,   p <- e_p p + sum_l W_p[l] r_l,
+// in the same summation order as a per-energy sweep.
+constexpr int kChunkRows = 128;
+template <int MODE>
+__global__ void __launch_bounds__(kChunkRows) chunk_apply_kernel(ChunkParams p) {
   typedef typename XUpd<MODE>::X X;
   typedef typename Ops<MODE>::HR HR;
   typedef HOps<HR> HO;
   typedef typename HO::H H;
-  const int i = blockIdx.x;
+  extern __shared__ unsigned char chunk_smem[];
+  const SolveDims& d = p.d;
   const int slot = blockIdx.y;
   const int hc = p.slots[slot].hcnt;
   if (hc <= 0) return;
-  const SolveDims& d = p.d;
-  __shared__ H Whx[kMaxHist], Whp[kMaxHist];
-  __shared__ double2 ex, ep;
-  if (threadIdx.x == 0) {
-    const ShiftCoef* cf = p.coef + ((size_t)slot * d.K + i) * p.hist_len;
-    // backward recurrences: A_l = ca_l + cb_{l+1} A_{l+1},  B_l = cb_{l+1} B_{l+1}  (B_{hc-1} = 1);
-    // W_x[l] = A_l cr_l, W_p[l] = B_l cr_l, e_x = cb_0 A_0, e_p = cb_0 B_0
-    double2 A = cf[hc - 1].ca, B = make_double2(1.0, 0.0);
-    Whx[hc - 1] = HO::from(cmul(A, cf[hc - 1].cr));
-    Whp[hc - 1] = HO::from(cmul(B, cf[hc - 1].cr));
-    for (int l = hc - 2; l >= 0; --l) {
-      A = cadd(cf[l].ca, cmul(cf[l + 1].cb, A));
-      B = cmul(cf[l + 1].cb, B);
-      Whx[l] = HO::from(cmul(A, cf[l].cr));
-      Whp[l] = HO::from(cmul(B, cf[l].cr));
-    }
-    ex = cmul(cf[0].cb, A);
-    ep = cmul(cf[0].cb, B);
-    atomicAdd(&p.counters[0], (unsigned long long)hc);
-    if (i == 0) atomicAdd(&p.counters[2], 1ull);
-  }
-  __syncthreads();
-  X* x = reinterpret_cast<X*>(p.xbuf) + ((size_t)slot * d.K + i) * d.nb;
-  X* pp = reinterpret_cast<X*>(p.pbuf) + ((size_t)slot * d.K + i) * d.nb;
+  const int tid = threadIdx.x, row = blockIdx.x * kChunkRows + tid;
+  if (row >= d.nb) return;   // no barrier below: every thread works on its own row only
+  H* hs = reinterpret_cast<H*>(chunk_smem);
   const H* h = reinterpret_cast<const H*>(p.rhist) + (size_t)slot * p.hist_len * d.nb;
-  const double2 exl = ex, epl = ep;
-  for (int row = threadIdx.x; row < d.nb; row += blockDim.x) {
+  for (int l = 0; l < hc; ++l) hs[l * kChunkRows + tid] = h[(size_t)l * d.nb + row];
+  const H* W = reinterpret_cast<const H*>(p.wbuf) + (size_t)slot * d.K * 2 * p.hist_len;
+  const double2* E = p.ebuf + (size_t)slot * d.K * 2;
+  X* x = reinterpret_cast<X*>(p.xbuf) + (size_t)slot * d.K * d.nb + row;
+  X* pp = reinterpret_cast<X*>(p.pbuf) + (size_t)slot * d.K * d.nb + row;
+  for (int i = 0; i < d.K; ++i) {
+    const H* Wx = W + (size_t)i * 2 * p.hist_len;
+    const H* Wp = Wx + p.hist_len;
     H sx = HO::zero(), sp = HO::zero();
     for (int l = 0; l < hc; ++l) {
-      const H r = h[(size_t)l * d.nb + row];
-      sx = HO::mac(Whx[l], r, sx);
-      sp = HO::mac(Whp[l], r, sp);
+      const H r = hs[l * kChunkRows + tid];
+      sx = HO::mac(Wx[l], r, sx);
+      sp = HO::mac(Wp[l], r, sp);
     }
-    const X xo = x[row], po = pp[row];
-    x[row] = XUpd<MODE>::upd(xo, exl, po, sx);
-    pp[row] = XUpd<MODE>::upd(X(), epl, po, sp);
+    const size_t o = (size_t)i * d.nb;
+    const X xo = x[o], po = pp[o];
+    x[o] = XUpd<MODE>::upd(xo, E[2 * i], po, sx);
+    pp[o] = XUpd<MODE>::upd(X(), E[2 * i + 1], po, sp);
   }
 }
 
@@ -1913,6 +1939,9 @@ cudaError_t kernels_init() {
   RSFD_ATTR(RSFD_DF64, 1)
   RSFD_ATTR(RSFD_DF64, 2)
 #undef RSFD_ATTR
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 #define RSFD_ATTR_B(R, B)                                                                                \
   if (e == cudaSuccess)                                                                                 \
     e = cudaFuncSetAttribute(passu_kernel<RSFD_DF64, R, 1, passu_budget_threads(B)>,                    \
@@ -2013,10 +2042,21 @@ cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, i
   p.coef = b.coef;
   p.counters = b.counters;
   p.hist_len = hist_len;
-  dim3 grid(d.K, d.W), block(256);
-  if (prec == RSFD_FP64) chunk_kernel<RSFD_FP64><<<grid, block, 0, st>>>(p);
-  else if (prec == RSFD_MIXED) chunk_kernel<RSFD_MIXED><<<grid, block, 0, st>>>(p);
-  else chunk_kernel<RSFD_DF64><<<grid, block, 0, st>>>(p);
+  p.wbuf = b.cwbuf;
+  p.ebuf = b.cebuf;
+  const int nct = (d.W * d.K + 255) / 256;
+  dim3 grid((d.nb + kChunkRows - 1) / kChunkRows, d.W);
+  const size_t smem = (size_t)hist_len * kChunkRows * (prec == RSFD_FP64 ? 16 : 8);
+  if (prec == RSFD_FP64) {
+    chunk_coef_kernel<RSFD_FP64><<<nct, 256, 0, st>>>(p);
+    chunk_apply_kernel<RSFD_FP64><<<grid, kChunkRows, smem, st>>>(p);
+  } else if (prec == RSFD_MIXED) {
+    chunk_coef_kernel<RSFD_MIXED><<<nct, 256, 0, st>>>(p);
+    chunk_apply_kernel<RSFD_MIXED><<<grid, kChunkRows, smem, st>>>(p);
+  } else {
+    chunk_coef_kernel<RSFD_DF64><<<nct, 256, 0, st>>>(p);
+    chunk_apply_kernel<RSFD_DF64><<<grid, kChunkRows, smem, st>>>(p);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reset_hist_kernel<<<(d.W + 255) / 256, 256, 0, st>>>(b.slots, d.W);

@@ -62,6 +62,7 @@ struct Handle {
   // solver workspace
   DevBuf rbuf, xbuf, pbuf, rhist, coef, eflag, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
   DevBuf pw, pcorr, pdots, ptickets;   // projector term of the solve
+  DevBuf cw, ce;                       // collapse weights and factors of the shift update
   CUtensorMap tmR, tmV;
   // dyson / transmission workspace
   DevBuf dy[8];
@@ -138,7 +139,7 @@ static void free_all(Handle* h) {
   DevBuf* bufs[] = {&h->rbuf,  &h->xbuf,      &h->pbuf,      &h->rhist,    &h->coef,
                     &h->eflag, &h->slots,     &h->shifts,    &h->partials, &h->tickets,
                     &h->Z,     &h->init_list, &h->init_grid, &h->counters, &h->pw,
-                    &h->pcorr, &h->pdots,     &h->ptickets,  &h->sweep};
+                    &h->pcorr, &h->pdots,     &h->ptickets,  &h->sweep, &h->cw, &h->ce};
   for (DevBuf* b : bufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -689,6 +690,8 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   if ((s = ensure(h, h->pbuf, (size_t)W * K * h->nr * vsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->rhist, (size_t)W * C * h->nr * hsz)) != RSFD_OK) return s;
   if ((s = ensure(h, h->coef, (size_t)W * K * C * sizeof(ShiftCoef))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->cw, (size_t)W * K * 2 * C * hsz)) != RSFD_OK) return s;
+  if ((s = ensure(h, h->ce, (size_t)W * K * 2 * sizeof(double2))) != RSFD_OK) return s;
   if ((s = ensure(h, h->eflag, 16)) != RSFD_OK) return s;
   if ((s = ensure(h, h->slots, (size_t)W * sizeof(SlotState))) != RSFD_OK) return s;
   if ((s = ensure(h, h->shifts, (size_t)W * K * sizeof(ShiftState))) != RSFD_OK) return s;
@@ -706,6 +709,8 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   b.pbuf = h->pbuf.p;
   b.rhist = h->rhist.p;
   b.coef = (ShiftCoef*)h->coef.p;
+  b.cwbuf = h->cw.p;
+  b.cebuf = (double2*)h->ce.p;
   b.error_flag = (int*)h->eflag.p;
   b.tmR = &h->tmR;
   b.tmV = &h->tmV;

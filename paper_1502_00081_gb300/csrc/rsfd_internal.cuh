@@ -124,6 +124,8 @@ struct SolverBuffers {
   void* pbuf;             // [W][K][nb] boundary rows of p^(i)
   void* rhist;            // [W][hist_len][nb] boundary rows of r_n (hi parts)
   ShiftCoef* coef;        // [W][K][hist_len]
+  void* cwbuf;            // [W][K][2][hist_len] collapse weights W_x, W_p (H type)
+  double2* cebuf;         // [W][K][2] collapse factors e_x, e_p
   int* error_flag;        // set by a kernel whose bounded wait expired
   const CUtensorMap* tmR; // TMA map of rbuf
   const CUtensorMap* tmV; // TMA map of the potential
