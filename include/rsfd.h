@@ -155,8 +155,9 @@ typedef struct {
   double ms_pass;             /* summed duration of stencil/seed-update launches (profile = 1) */
   double ms_shift;            /* summed duration of the collapsed shift-update launches (profile = 1) */
   int64_t n_pass;             /* stencil/seed-update launches */
-  int64_t n_shift;            /* collapsed shift-update launches */
-  int64_t n_other;            /* other kernel launches (slot set-up, reductions) */
+  int64_t n_shift;            /* collapsed shift-update launches (the apply kernel) */
+  int64_t n_other;            /* other kernel launches (collapse coefficients, history reset, projector
+                                 terms, slot set-up, write-out) */
   int64_t slot_iterations;    /* sum over columns of seed iterations */
   int64_t shift_updates;      /* recorded (column, energy, iteration) updates applied */
   int64_t shift_slot_chunks;  /* (column, collapse) pairs: each reads and writes x_b, p_b of K energies once */

@@ -849,7 +849,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
     }
     h->stats.n_pass += C;
     h->stats.n_shift += 1;
-    h->stats.n_other += 1 + (b.n_atoms > 0 ? 2 * C : 0);
+    h->stats.n_other += 2 + (b.n_atoms > 0 ? 2 * C : 0);   // collapse coefficients, history reset, projectors
     RSFD_CK(h, cudaMemcpyAsync(hs.data(), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
     RSFD_CK(h, cudaMemcpyAsync(&herr, b.error_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     RSFD_CK(h, cudaStreamSynchronize(st));
