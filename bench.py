@@ -456,7 +456,7 @@ def run_precision_speedup(args):
     """Reduced-precision forms against the plain FP64 GPU form on the full pipeline (G0_bb for every
     boundary column, Dyson, T), where the transmission can be compared: a 16x16x48 grid (h = 0.4,
     4th order, 6 wells, two boundary planes per side), 16 energies in [0.3, 1.0] Ha, eta = 1e-3 and
-    1e-2.  Every form runs at the same stopping tolerance (1e-6); accuracy is judged against an FP64
+    1e-2.  Every form runs at the same stopping tolerance (1e-6); accuracy is measured against an FP64
     run at tol 1e-10, and the speedup over the FP64 form at tol 1e-6 is reported where |dT| <= 1e-4
     and the G_bb error <= 1e-5 hold.  One JSON line per (eta, precision)."""
     import torch
