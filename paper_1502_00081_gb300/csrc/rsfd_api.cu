@@ -14,6 +14,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <exception>
+#include <new>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -304,7 +306,7 @@ static uint64_t fnv1a(uint64_t hv, const void* p, size_t n) {
 
 extern "C" {
 
-rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int32_t fd_order, int32_t n_face,
+static rsfd_status rsfd_create_impl(rsfd_handle* out, const int32_t grid[3], double hh, int32_t fd_order, int32_t n_face,
                         const double* V_loc, const rsfd_projectors* proj, int32_t precision, void* stream) {
   if (!out) return fail(nullptr, RSFD_ERR_ARG, "rsfd_create: out is NULL");
   *out = nullptr;
@@ -493,14 +495,14 @@ rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int3
   return RSFD_OK;
 }
 
-rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows) {
+static rsfd_status rsfd_boundary_rows_impl(rsfd_handle h, int32_t* nb, int64_t* rows) {
   if (!h || !nb) return fail(h, RSFD_ERR_ARG, "rsfd_boundary_rows: NULL argument");
   *nb = h->nb;
   if (rows) memcpy(rows, h->brow.data(), h->nb * sizeof(int64_t));
   return RSFD_OK;
 }
 
-rsfd_status rsfd_set_tracked_planes(rsfd_handle h, int32_t n, const int32_t* z) {
+static rsfd_status rsfd_set_tracked_planes_impl(rsfd_handle h, int32_t n, const int32_t* z) {
   if (!h) return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: NULL handle");
   if (n < 0 || n > RSFD_MAX_TRACKED_PLANES || (n > 0 && !z))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_tracked_planes: need 0 <= n <= " + std::to_string(RSFD_MAX_TRACKED_PLANES));
@@ -519,7 +521,7 @@ rsfd_status rsfd_set_tracked_planes(rsfd_handle h, int32_t n, const int32_t* z) 
   return RSFD_OK;
 }
 
-rsfd_status rsfd_tracked_rows(rsfd_handle h, int32_t* nr, int64_t* rows) {
+static rsfd_status rsfd_tracked_rows_impl(rsfd_handle h, int32_t* nr, int64_t* rows) {
   if (!h || !nr) return fail(h, RSFD_ERR_ARG, "rsfd_tracked_rows: NULL argument");
   *nr = h->nr;
   if (rows) {
@@ -531,7 +533,7 @@ rsfd_status rsfd_tracked_rows(rsfd_handle h, int32_t* nr, int64_t* rows) {
   return RSFD_OK;
 }
 
-rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
+static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_opts* o) {
   if (!h) return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: NULL handle");
   if (!o) {
     memset(&h->opts, 0, sizeof(h->opts));
@@ -574,13 +576,13 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
   return RSFD_OK;
 }
 
-rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out) {
+static rsfd_status rsfd_get_stats_impl(rsfd_handle h, rsfd_stats* out) {
   if (!h || !out) return fail(h, RSFD_ERR_ARG, "rsfd_get_stats: NULL argument");
   *out = h->stats;
   return RSFD_OK;
 }
 
-rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
                               double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
                               void* G0_bb, rsfd_col_info* info, double* final_res) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg: NULL handle");
@@ -935,7 +937,7 @@ rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols,
   return worst;
 }
 
-rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+static rsfd_status rsfd_dyson_boundary_impl(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
                                 int32_t K, void* G_bb, double* refine_residual) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_boundary: NULL handle");
   if (!G0_bb || !Sigma_L || !Sigma_R || !G_bb || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_boundary: bad arguments");
@@ -943,7 +945,7 @@ rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Si
   return dyson_run(h, G0_bb, Sigma_L, Sigma_R, K, G_bb, refine_residual);
 }
 
-rsfd_status rsfd_dyson_tracked(rsfd_handle h, const void* G0, const void* Sigma_L, const void* Sigma_R, int32_t K,
+static rsfd_status rsfd_dyson_tracked_impl(rsfd_handle h, const void* G0, const void* Sigma_L, const void* Sigma_R, int32_t K,
                                void* G, double* refine_residual) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_tracked: NULL handle");
   if (!G0 || !Sigma_L || !Sigma_R || !G || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_dyson_tracked: bad arguments");
@@ -951,14 +953,14 @@ rsfd_status rsfd_dyson_tracked(rsfd_handle h, const void* G0, const void* Sigma_
   return dyson_tracked_run(h, h->nr, G0, Sigma_L, Sigma_R, K, G, refine_residual);
 }
 
-rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,
+static rsfd_status rsfd_transmission_impl(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,
                               double* T) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_transmission: NULL handle");
   if (!G_bb || !Sigma_L || !Sigma_R || !T || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_transmission: bad arguments");
   return transmission_run(h, G_bb, Sigma_L, Sigma_R, K, T);
 }
 
-rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double hh, int32_t fd_order, const double* energies,
+static rsfd_status rsfd_lead_sigma_uniform_impl(int32_t Nx, int32_t Ny, double hh, int32_t fd_order, const double* energies,
                                     double eta, int32_t K, double* Sigma_L, double* Sigma_R) {
   if (Nx < 1 || Ny < 1 || !(hh > 0) || (fd_order != 2 && fd_order != 4) || !energies || K < 1 || !Sigma_L ||
       !Sigma_R || !(eta > 0))
@@ -1001,7 +1003,7 @@ struct TuneKey {
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<rsfd_solve_opts, double>> g_tune_cache;
 
-rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
+static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
                           rsfd_solve_opts* best, double* us_per_slot_iteration) {
   if (!h || !energies || K < 1 || !(eta > 0) || slots < 1 || iters < 1)
     return fail(h, RSFD_ERR_ARG, "rsfd_autotune: bad argument");
@@ -1111,7 +1113,7 @@ rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, doub
 // region drives that region's iteration chunks (CUDA graphs) on the handle's own stream, so the
 // regions' kernels run concurrently on the device and small regions fill the SMs that large ones
 // leave idle.  The worst status is returned; each job's own status is stored in the job.
-rsfd_status rsfd_shifted_cocg_regions(int32_t n, rsfd_region_solve* jobs) {
+static rsfd_status rsfd_shifted_cocg_regions_impl(int32_t n, rsfd_region_solve* jobs) {
   if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_regions: bad job list");
   for (int i = 0; i < n; ++i) {
     if (!jobs[i].h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg_regions: NULL handle in job " + std::to_string(i));
@@ -1175,7 +1177,7 @@ static uint64_t sweep_block_hash(const Handle* h, const int64_t* cols, int B, co
   return hv;
 }
 
-rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+static rsfd_status rsfd_shifted_cocg_sweep_impl(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
                                     int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
                                     rsfd_col_info* info, int32_t* blocks_resumed) {
@@ -1247,7 +1249,7 @@ rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t 
   return worst;
 }
 
-rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, const double* V_right,
+static rsfd_status rsfd_lead_sigma_decimation_impl(rsfd_handle h, const double* V_left, const double* V_right,
                                        const double* energies, int32_t K, double eta, int32_t maxit, void* Sigma_L,
                                        void* Sigma_R, int32_t* iterations) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_lead_sigma_decimation: NULL handle");
@@ -1269,7 +1271,7 @@ rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, cons
 // Energies k0 .. k0 + kcount - 1 of a completed checkpointed sweep, all columns, read from the block
 // files into a device buffer [kcount][ncols][nb]: the energy-chunked G0_bb of a sweep whose whole
 // G0_bb does not fit in device memory.
-rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+static rsfd_status rsfd_sweep_load_energies_impl(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
                                      int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
                                      int32_t seed_index, int32_t block, const char* dir, int32_t k0, int32_t kcount,
                                      void* G0_part) {
@@ -1309,5 +1311,98 @@ rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t
     fclose(f);
   }
   return RSFD_OK;
+}
+
+// Entry points: the implementations above, behind a guard that turns a host-side C++ exception (a
+// failed host allocation, above all) into a status code, so that none crosses the C ABI.
+#define RSFD_GUARD(h, call)                                                              \
+  try {                                                                                  \
+    return call;                                                                         \
+  } catch (const std::bad_alloc&) {                                                      \
+    return fail((h), RSFD_ERR_ALLOC, "host allocation failed");                         \
+  } catch (const std::exception& ex_) {                                                  \
+    return fail((h), RSFD_ERR_CUDA, std::string("internal error: ") + ex_.what());       \
+  } catch (...) {                                                                        \
+    return fail((h), RSFD_ERR_CUDA, "internal error");                                   \
+  }
+
+rsfd_status rsfd_create(rsfd_handle* out, const int32_t grid[3], double hh, int32_t fd_order, int32_t n_face,
+                        const double* V_loc, const rsfd_projectors* proj, int32_t precision, void* stream) {
+  RSFD_GUARD(nullptr, rsfd_create_impl(out, grid, hh, fd_order, n_face, V_loc, proj, precision, stream));
+}
+
+rsfd_status rsfd_boundary_rows(rsfd_handle h, int32_t* nb, int64_t* rows) {
+  RSFD_GUARD(h, rsfd_boundary_rows_impl(h, nb, rows));
+}
+
+rsfd_status rsfd_set_tracked_planes(rsfd_handle h, int32_t n, const int32_t* z) {
+  RSFD_GUARD(h, rsfd_set_tracked_planes_impl(h, n, z));
+}
+
+rsfd_status rsfd_tracked_rows(rsfd_handle h, int32_t* nr, int64_t* rows) {
+  RSFD_GUARD(h, rsfd_tracked_rows_impl(h, nr, rows));
+}
+
+rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* o) {
+  RSFD_GUARD(h, rsfd_set_solve_options_impl(h, o));
+}
+
+rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out) {
+  RSFD_GUARD(h, rsfd_get_stats_impl(h, out));
+}
+
+rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+                              double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
+                              void* G0_bb, rsfd_col_info* info, double* final_res) {
+  RSFD_GUARD(h, rsfd_shifted_cocg_impl(h, cols, ncols, energies, K, eta, tol, maxit, seed_kind, seed_index, G0_bb, info, final_res));
+}
+
+rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+                                int32_t K, void* G_bb, double* refine_residual) {
+  RSFD_GUARD(h, rsfd_dyson_boundary_impl(h, G0_bb, Sigma_L, Sigma_R, K, G_bb, refine_residual));
+}
+
+rsfd_status rsfd_dyson_tracked(rsfd_handle h, const void* G0, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                               void* G, double* refine_residual) {
+  RSFD_GUARD(h, rsfd_dyson_tracked_impl(h, G0, Sigma_L, Sigma_R, K, G, refine_residual));
+}
+
+rsfd_status rsfd_transmission(rsfd_handle h, const void* G_bb, const void* Sigma_L, const void* Sigma_R, int32_t K,
+                              double* T) {
+  RSFD_GUARD(h, rsfd_transmission_impl(h, G_bb, Sigma_L, Sigma_R, K, T));
+}
+
+rsfd_status rsfd_lead_sigma_uniform(int32_t Nx, int32_t Ny, double hh, int32_t fd_order, const double* energies,
+                                    double eta, int32_t K, double* Sigma_L, double* Sigma_R) {
+  RSFD_GUARD(nullptr, rsfd_lead_sigma_uniform_impl(Nx, Ny, hh, fd_order, energies, eta, K, Sigma_L, Sigma_R));
+}
+
+rsfd_status rsfd_autotune(rsfd_handle h, const double* energies, int32_t K, double eta, int32_t slots, int32_t iters,
+                          rsfd_solve_opts* best, double* us_per_slot_iteration) {
+  RSFD_GUARD(h, rsfd_autotune_impl(h, energies, K, eta, slots, iters, best, us_per_slot_iteration));
+}
+
+rsfd_status rsfd_shifted_cocg_regions(int32_t n, rsfd_region_solve* jobs) {
+  RSFD_GUARD(nullptr, rsfd_shifted_cocg_regions_impl(n, jobs));
+}
+
+rsfd_status rsfd_shifted_cocg_sweep(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                    int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                    int32_t seed_index, int32_t block, const char* dir, void* G0_bb,
+                                    rsfd_col_info* info, int32_t* blocks_resumed) {
+  RSFD_GUARD(h, rsfd_shifted_cocg_sweep_impl(h, cols, ncols, energies, K, eta, tol, maxit, seed_kind, seed_index, block, dir, G0_bb, info, blocks_resumed));
+}
+
+rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, const double* V_right,
+                                       const double* energies, int32_t K, double eta, int32_t maxit, void* Sigma_L,
+                                       void* Sigma_R, int32_t* iterations) {
+  RSFD_GUARD(h, rsfd_lead_sigma_decimation_impl(h, V_left, V_right, energies, K, eta, maxit, Sigma_L, Sigma_R, iterations));
+}
+
+rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                                     int32_t K, double eta, double tol, int32_t maxit, int32_t seed_kind,
+                                     int32_t seed_index, int32_t block, const char* dir, int32_t k0, int32_t kcount,
+                                     void* G0_part) {
+  RSFD_GUARD(h, rsfd_sweep_load_energies_impl(h, cols, ncols, energies, K, eta, tol, maxit, seed_kind, seed_index, block, dir, k0, kcount, G0_part));
 }
 }  // extern "C"
