@@ -22,7 +22,9 @@ Modules and the passages they follow:
 * ``leads``         -- lead self-energies (Eqs. self-energy,
                        surface green's function, sec2-01, sec2-02) for a
                        uniform V=0 finite-difference lead, by Bloch roots
-                       and by Sancho-Rubio decimation.
+                       and by Sancho-Rubio decimation, and for a lead that
+                       repeats one principal layer with its own potential
+                       (decimation).
 * ``dyson``         -- unperturbed -> perturbed boundary Green's function
                        (Eq. sec3-01a as a linear solve, and the block
                        formulas Eqs. sec3-02 ... sec3-06).
