@@ -65,7 +65,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     if force or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

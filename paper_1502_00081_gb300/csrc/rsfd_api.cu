@@ -1314,8 +1314,10 @@ static rsfd_status rsfd_sweep_load_energies_impl(rsfd_handle h, const int64_t* c
 }
 
 // Entry points: the implementations above, behind a guard that turns a host-side C++ exception (a
-// failed host allocation, above all) into a status code, so that none crosses the C ABI.
+// failed host allocation, above all) into a status code, so that none crosses the C ABI, and inside
+// an NVTX range named after the entry point (setup, solve, Dyson, transmission, ... in a profile).
 #define RSFD_GUARD(h, call)                                                              \
+  rsfd::NvtxRange nvtx_range_(__func__);                                                 \
   try {                                                                                  \
     return call;                                                                         \
   } catch (const std::bad_alloc&) {                                                      \

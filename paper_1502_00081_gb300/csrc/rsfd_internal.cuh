@@ -8,9 +8,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rsfd.h"
 
 namespace rsfd {
+
+// NVTX range over a scope (a named interval in an attached profiler's timeline; no effect otherwise)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------------------------
 // complex helpers: float2 / double2 with interleaved (re, im)
