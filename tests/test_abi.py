@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -79,3 +80,22 @@ def test_sweep_rejects_bad_arguments_without_gpu(lib):
     # NULL handle, then a NULL directory: both rejected before any device work
     assert L.rsfd_shifted_cocg_sweep(None, cols, 2, en, 1, 1e-2, 1e-8, 10, 0, 0, 1, b"/tmp", 1, info, None) == 1
     assert L.rsfd_shifted_cocg_regions(-1, None) == 1
+
+
+def test_missing_library_fails_loudly(repo_root):
+    """Without librsfd.so the binding raises instead of computing anything elsewhere (there is no CPU
+    fallback for any entry point)."""
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_1502_00081_gb300.binding as b\n"
+        "b._LIB = None\n"
+        "b.lib_path = lambda: '/nonexistent/librsfd.so'\n"
+        "import numpy as np\n"
+        "try:\n"
+        "    b.rsfd_create((4, 4, 6), 0.5, 2, np.zeros(96))\n"
+        "except ImportError as e:\n"
+        "    print('raised', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(1)\n" % repo_root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0 and "raised" in r.stdout, r.stdout + r.stderr
