@@ -369,18 +369,20 @@ rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, cons
 #define RSFD_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* Allocation-free Dyson step.  The paper has no counterpart: this entry point exists for callers
- * that cannot allocate device memory when they need the step, e.g. code recording a CUDA graph
- * (no cudaMalloc during stream capture), a service whose device memory is already handed to
- * another allocator, or a library that must not change the device's allocation state.
+ * that cannot allocate device memory when they need the step, e.g. a service or framework that has
+ * handed its whole device-memory budget to its own caching allocator up front, or a plug-in whose
+ * host application forbids it to change the device's allocation state.
  *
  * It computes the same result as rsfd_dyson_boundary for FP64 data, without a handle:
  *   (I - G0_bb(k) Sigma_bb(k)) G_bb(k) = G0_bb(k),  k < K,  with two FP64 refinement steps.
  *   nb      even, the number of boundary rows (ns = nb/2 per slab).
+ *   K       1 .. 65535 energies.
  *   G0_bb   device [K][nb][nb] c128, column-major per energy (same layout as rsfd_dyson_boundary).
  *   Sigma_L, Sigma_R  device [K][ns][ns] c128.
  *   G_bb    device output [K][nb][nb] c128 (may not alias G0_bb).
  *   refine_residual  host [K] (nullable): ||G0 - M G||_F / ||G0||_F.
- *   stream  cudaStream_t (NULL = legacy default stream); the call synchronises it.
+ *   stream  cudaStream_t (NULL = legacy default stream).  The call ends by copying its status word
+ *           and the residuals to the host and synchronising this stream.
  * Scratch: a static __device__ array of RSFD_NOALLOC_SCRATCH_BYTES (32 MiB) held by every GPU that
  * loads the library until the process exits.  The call needs 3*nb*nb*K*16 bytes plus pivots and
  * returns RSFD_ERR_ARG (with a message naming the limit) when that exceeds the array; for nb = 128
@@ -390,7 +392,8 @@ rsfd_status rsfd_lead_sigma_decimation(rsfd_handle h, const double* V_left, cons
  * Sharing: every call, on any stream, uses the same array and it keeps the previous call's
  * contents (the call clears what must start at zero); calls that overlap on the GPU race with
  * each other, so serialise them.
- * Returns RSFD_OK, RSFD_ERR_ARG, RSFD_ERR_CUDA, or RSFD_ERR_BREAKDOWN (singular I - G0 Sigma). */
+ * Returns RSFD_OK, RSFD_ERR_ARG, RSFD_ERR_CUDA, or RSFD_ERR_BREAKDOWN (singular I - G0 Sigma; the
+ * message names the first such energy, as rsfd_dyson_boundary's does). */
 rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L,
                                         const void* Sigma_R, void* G_bb, double* refine_residual, void* stream);
 

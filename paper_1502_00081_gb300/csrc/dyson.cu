@@ -855,9 +855,9 @@ rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const voi
 // Allocation-free variant of the Dyson step.
 //
 // Some callers cannot allocate device memory at the point where they need the Dyson step: a
-// program that is recording a CUDA graph (cudaMalloc is not allowed while a stream is being
-// captured), a service that has handed its whole device-memory budget to another allocator up
-// front, or a library that must not change the device's allocation state.  For them,
+// service or framework that has handed its whole device-memory budget to its own caching allocator
+// up front (a cudaMalloc then fails, or would take memory that allocator counts on), or a plug-in
+// that a host application forbids to change the device's allocation state.  For them,
 // rsfd_dyson_boundary_noalloc keeps its scratch (the matrices I - G0 Sigma and their LU factors,
 // the refinement residual, the pivots) in the file-scope device array below, which exists for as
 // long as the library is loaded on every GPU that loaded it.  The caller passes the inputs and the
@@ -874,26 +874,32 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 static void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
+// first singular energy: *bad starts at K (none) and takes the smallest k with a zero pivot, so the
+// message names the same energy as rsfd_dyson_boundary's
 __global__ void noalloc_finish(const int* info, const double* red, int K, int* bad, double* ratio) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    if (info[k] != 0) atomicMax(bad, k + 1);
+    if (info[k] != 0) atomicMin(bad, k);
     const double g = red[K + k] > 0 ? red[K + k] : 1.0;
     ratio[k] = sqrt(red[k]) / sqrt(g);
   }
 }
 
+__global__ void fill_int(int* p, int v) { *p = v; }
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-}  // namespace rsfd
-
-extern "C" rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L,
-                                                   const void* Sigma_R, void* G_bb, double* refine_residual,
-                                                   void* stream) {
-  using namespace rsfd;
+// Body of rsfd_dyson_boundary_noalloc (the C entry point in rsfd_api.cu wraps it in the ABI's
+// exception guard).
+rsfd_status dyson_noalloc_run(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+                              void* G_bb, double* refine_residual, void* stream) {
   if (nb < 2 || (nb % 2) != 0 || K < 1 || !G0_bb || !Sigma_L || !Sigma_R || !G_bb || G0_bb == G_bb)
     return handle_fail(nullptr, RSFD_ERR_ARG, "rsfd_dyson_boundary_noalloc: bad arguments");
+  // the batched kernels put the energy on gridDim.y / gridDim.z
+  if (K > 65535)
+    return handle_fail(nullptr, RSFD_ERR_ARG,
+                       "rsfd_dyson_boundary_noalloc: K = " + std::to_string(K) + " exceeds the limit of 65535 energies per call");
   const long long n2 = (long long)nb * nb;
   const size_t need = 3 * align256((size_t)n2 * K * sizeof(double2)) + align256((size_t)K * (nb + 1) * sizeof(int)) +
                       align256((size_t)3 * K * sizeof(double)) + align256(sizeof(int));
@@ -933,8 +939,8 @@ extern "C" rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const 
   const double2 m1 = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
   // the scratch keeps the previous call's contents: clear the flags that must start at zero
   e = cudaMemsetAsync(info, 0, K * sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
   if (e != cudaSuccess) return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  fill_int<<<1, 1, 0, st>>>(bad, K);
   set_identity<<<grid_for(tot), 256, 0, st>>>(dM, nb, K);
   const int ns = nb / 2;
   zgemm(st, K, nb, ns, ns, m1, G0, nb, n2, 0, (const double2*)Sigma_L, ns, (long long)ns * ns, one, dM, nb, n2);
@@ -957,14 +963,16 @@ extern "C" rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const 
   frob2_batched<<<K, 256, 0, st>>>(G0, n2, red + K);
   noalloc_finish<<<1, 256, 0, st>>>(info, red, K, bad, red + 2 * K);
   e = cudaGetLastError();
-  int hbad = 0;
+  int hbad = K;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && refine_residual)
     e = cudaMemcpyAsync(refine_residual, red + 2 * K, K * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return handle_fail(nullptr, RSFD_ERR_CUDA, std::string("rsfd_dyson_boundary_noalloc: ") + cudaGetErrorString(e));
-  if (hbad)
+  if (hbad < K)
     return handle_fail(nullptr, RSFD_ERR_BREAKDOWN,
-                       "rsfd_dyson_boundary_noalloc: singular I - G0 Sigma at energy " + std::to_string(hbad - 1));
+                       "rsfd_dyson_boundary_noalloc: singular I - G0 Sigma at energy " + std::to_string(hbad));
   return RSFD_OK;
 }
+
+}  // namespace rsfd

@@ -1407,4 +1407,9 @@ rsfd_status rsfd_sweep_load_energies(rsfd_handle h, const int64_t* cols, int32_t
                                      void* G0_part) {
   RSFD_GUARD(h, rsfd_sweep_load_energies_impl(h, cols, ncols, energies, K, eta, tol, maxit, seed_kind, seed_index, block, dir, k0, kcount, G0_part));
 }
+
+rsfd_status rsfd_dyson_boundary_noalloc(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L,
+                                        const void* Sigma_R, void* G_bb, double* refine_residual, void* stream) {
+  RSFD_GUARD(nullptr, rsfd::dyson_noalloc_run(nb, K, G0_bb, Sigma_L, Sigma_R, G_bb, refine_residual, stream));
+}
 }  // extern "C"

@@ -244,6 +244,8 @@ rsfd_status dyson_tracked_run(Handle* h, int nr, const void* G0, const void* SL,
 rsfd_status transmission_run(Handle* h, const void* G, const void* SL, const void* SR, int K, double* T);
 rsfd_status lead_decimation_run(Handle* h, const double* VL, const double* VR, const double* E, int K, double eta,
                                 int maxit, void* SL, void* SR, int* iters);
+rsfd_status dyson_noalloc_run(int32_t nb, int32_t K, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,
+                              void* G_bb, double* refine_residual, void* stream);
 
 // Host lead self-energy (lead_sigma.cpp).
 rsfd_status lead_sigma_uniform(int nx, int ny, double h, int fd_order, const double* E, double eta, int K,

@@ -99,3 +99,15 @@ def test_missing_library_fails_loudly(repo_root):
         "sys.exit(1)\n" % repo_root)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert r.returncode == 0 and "raised" in r.stdout, r.stdout + r.stderr
+
+
+def test_noalloc_dyson_rejects_bad_arguments_without_gpu(lib):
+    """The allocation-free Dyson entry point checks its sizes before any device work: an odd nb, and
+    more energies than its batched kernels' grid can hold (gridDim.y / gridDim.z <= 65535)."""
+    rs, _ = lib
+    L = rs.load_library()
+    fake = ctypes.c_void_p(256)   # never dereferenced: the calls fail in their argument checks
+    out = ctypes.c_void_p(512)
+    assert L.rsfd_dyson_boundary_noalloc(3, 1, fake, fake, fake, out, None, None) == 1
+    assert L.rsfd_dyson_boundary_noalloc(2, 70000, fake, fake, fake, out, None, None) == 1
+    assert "65535" in rs.rsfd_last_error(None)

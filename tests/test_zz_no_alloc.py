@@ -1,8 +1,8 @@
 """The allocation-free Dyson entry point (rsfd_dyson_boundary_noalloc) against the handle-based one.
 
-Callers that cannot allocate device memory (for instance while a CUDA graph is being recorded, or
-when another allocator owns the device's memory) use rsfd_dyson_boundary_noalloc, whose scratch is a
-static device array inside the library.  This test calls it through the C ABI twice in a row, with
+Callers that cannot allocate device memory (a service whose device memory already belongs to its own
+caching allocator, or a plug-in whose host application forbids new allocations) use
+rsfd_dyson_boundary_noalloc, whose scratch is a static device array inside the library.  This test calls it through the C ABI twice in a row, with
 different inputs, and compares each result with rsfd_dyson_boundary (which allocates its workspace
 through its handle) within the tolerance the Dyson tests use.  The second call checks that contents
 left in the shared scratch by the first call do not leak into the next result.  The file is named so
