@@ -147,6 +147,13 @@ typedef struct {
   int32_t tile_x;         /* RSFD_PASS_STORED, double-float, one row per thread: tile width in x, 0 or 32
                              (one tile row per warp) or 16 (two tile rows per warp; less idle work when Nx
                              is an odd multiple of 16, e.g. 48 or 80); tile_y must be even */
+  int32_t wait_cap;       /* attempts of a pass's bounded wait for its TMA transfers before the wait is
+                             declared lost (each attempt sleeps up to 1 ms): 0 = 4096; -1 = none, so every
+                             CTA's first wait expires at once (a test of the RSFD_ERR_TIMEOUT path: the CTA
+                             still drains its issued transfers with the full cap before it returns) */
+  double breakdown_tol;   /* quasi-null test of the seed's (r_n, r_n): breakdown when |(r,r)| <= this times
+                             ||r||^2 (or <= 1e-300); 0 = 1e-28.  A large value makes every column report
+                             RSFD_ERR_BREAKDOWN (a test of that path) */
 } rsfd_solve_opts;
 
 /* Counters of the last rsfd_shifted_cocg call. */

@@ -60,7 +60,7 @@ class rsfd_solve_opts(ctypes.Structure):
                 ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
                 ("dyson_kind", ctypes.c_int32), ("dyson_refine", ctypes.c_int32), ("reg_budget", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32)]
+                ("tile_x", ctypes.c_int32), ("wait_cap", ctypes.c_int32), ("breakdown_tol", ctypes.c_double)]
 
 
 class rsfd_region_solve(ctypes.Structure):
@@ -253,11 +253,11 @@ def rsfd_boundary_rows(h):
 
 def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0,
                            pass_kind=0, prefetch=0, rows_per_thread=0, dyson_kind=0, dyson_refine=0, reg_budget=0,
-                           tile_x=0):
+                           tile_x=0, wait_cap=0, breakdown_tol=0.0):
     lib = load_library()
     o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile),
                         int(pass_kind), int(prefetch), int(rows_per_thread), int(dyson_kind), int(dyson_refine),
-                        int(reg_budget), int(tile_x))
+                        int(reg_budget), int(tile_x), int(wait_cap), float(breakdown_tol))
     _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
 
 

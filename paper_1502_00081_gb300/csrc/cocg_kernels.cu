@@ -537,11 +537,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase with the given parity; false when the cap is reached.  Each try_wait
+// Bounded wait for the phase with the given parity; false when the cap is reached (cap attempts).  Each try_wait
 // carries a suspend-time hint, so a waiting thread sleeps until the phase completes (or the hint
 // expires) instead of spinning through issue slots.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitCap; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long cap = kWaitCap) {
+  for (long long i = 0; i < cap; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -553,6 +553,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
   }
   return false;
+}
+// attempts of a pass's first wait on each bundle (the solve's wait_cap option; drains keep kWaitCap)
+__device__ __forceinline__ long long first_wait_cap(const SolveDims& d) {
+  return d.wait_cap == 0 ? kWaitCap : (d.wait_cap < 0 ? 0ll : (long long)d.wait_cap);
 }
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
@@ -734,7 +738,7 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
         }
         const double rabs = sqrt(cabs2(rr));
         const double nrm2s = S.nrm2 * cabs2(scale_n);
-        if (!(rabs > 1e-300) || rabs <= 1e-28 * nrm2s) {
+        if (!(rabs > 1e-300) || rabs <= p.d.brk_tol * nrm2s) {
           st->status = SLOT_BREAKDOWN;
           S.stop = 1;
         } else {
@@ -1001,7 +1005,7 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
       issue(s + kDepth);
       issued = s + kDepth + 1;
     }
-    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
+    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par, first_wait_cap(p.d))) {
       s_abort[s & 1] = 1;
       atomicExch(p.error_flag, 1);
     }
@@ -1294,7 +1298,7 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
       issue(s + kDepth);
       issued = s + kDepth + 1;
     }
-    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par)) {
+    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par, first_wait_cap(p.d))) {
       s_abort[s & 1] = 1;
       atomicExch(p.error_flag, 1);
     }

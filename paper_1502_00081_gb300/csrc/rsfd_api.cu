@@ -572,6 +572,9 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: dyson_refine must be 0 .. 8");
   if (o->iters_per_sync > kMaxHist)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: iters_per_sync must be <= " + std::to_string(kMaxHist));
+  if (o->wait_cap < -1) return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: wait_cap must be >= -1");
+  if (!(o->breakdown_tol >= 0.0) || !isfinite(o->breakdown_tol))
+    return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: breakdown_tol must be finite and >= 0");
   h->opts = *o;
   return RSFD_OK;
 }
@@ -630,6 +633,8 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
   d.regs = (prec == RSFD_DF64 && d.rows == 1 && d.kind == RSFD_PASS_STORED) ? h->opts.reg_budget : 0;
   d.tile_x = (h->opts.tile_x == 16 && d.kind == RSFD_PASS_STORED) ? 16 : 32;
+  d.wait_cap = h->opts.wait_cap;
+  d.brk_tol = h->opts.breakdown_tol > 0.0 ? h->opts.breakdown_tol : 1e-28;
   if (!tile_ok(prec, h->R, d.tile_y, d.kind, d.rows, d.regs, d.tile_x))
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: invalid tile_y / tile_x");
   // TMA prefetch depth: the option, else the deepest that fits in shared memory (fused pass: a CTA

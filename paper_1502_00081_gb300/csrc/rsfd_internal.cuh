@@ -122,6 +122,8 @@ struct SolveDims {
   int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
   int regs;           // register budget of the one-row double-float pass (0, 1)
   int tile_x;         // stored-product pass tile width in x: 32, or 16 (one-row double-float pass)
+  int wait_cap;       // attempts of the passes' first TMA waits: 0 = default, < 0 = none (test)
+  double brk_tol;     // quasi-null threshold of (r, r) relative to ||r||^2
 };
 
 struct Handle;   // defined in rsfd_api.cu

@@ -236,3 +236,18 @@ def test_double_float_sixteen_wide_tiles(rs, grid, order, tile_y):
     assert relf(outs[0][0], outs[1][0]) <= 1e-6
     # near the double-float floor the iteration count follows the rounding of the dots (a few per cent)
     assert (np.abs(outs[0][1] - outs[1][1]) <= 0.05 * outs[1][1]).all()
+
+
+@pytest.mark.parametrize("grid", [(64, 18, 16), (40, 20, 18)])
+def test_double_float_bench_shape_fourth_order(rs, grid):
+    """The launch shape of the benchmarked 64x64x128 run (stored pass, 32 x 16 tile, one row per thread,
+    the whole z extent per CTA, 96-register variant) on a 4th-order (R = 2) grid with seed switching:
+    full x tiles and ragged x, y tiles, against the FP64 oracle."""
+    p = small_problem(grid=grid, h=0.4, fd_order=4, n_wells=6, n_energies=6, e_range=(-0.5, 0.5),
+                      eta=5e-2, tol=1e-10, cols=2, n_face=1)
+    opts = dict(pass_kind=2, tile_y=16, rows_per_thread=1, z_chunk=grid[2], tile_x=32, reg_budget=0, slots=2)
+    st, G, info, res, _ = gpu_g0(rs, p, rs.RSFD_DF64, opts=opts)
+    assert st == rs.RSFD_OK
+    Go, ores = shifted_cocg_columns(p, tol=1e-12)
+    assert relf(G, Go) <= 1e-6
+    assert max(r.switches for r in ores) >= 1

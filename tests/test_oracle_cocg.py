@@ -193,3 +193,32 @@ def test_planted_recurrence_mistakes_are_caught(old, new):
     p = small_problem(grid=(4, 4, 6), h=0.5, fd_order=2, n_wells=2, n_energies=4, eta=3e-2)
     assert _shifted_err(p, None) < 1e-8
     assert _shifted_err(p, "planted", _planted_module(old, new)) > 1e-4
+
+
+def test_breakdown_branch_on_a_quasi_null_right_hand_side():
+    """b = e_j + i e_k has b^T b = 1 + i^2 = 0 with b != 0: the unconjugated form of COCG vanishes at
+    the start, which the oracle must report as a breakdown (reading 5) instead of dividing by it.  A
+    conjugated form (b^H b = 2) would not break down, and a right-hand side that is not quasi-null
+    (b = e_j + 0.5 i e_k) must converge to the dense solution as usual."""
+    p = small_problem(grid=(5, 4, 6), h=0.5, fd_order=2, n_wells=2, n_energies=4, eta=5e-2, tol=1e-10)
+    H, P, wE = hamiltonian(p)
+    Z = p.energies + 1j * p.eta
+    f = lambda v: apply_h(H, P, wE, v)
+    j, k = 3, 17
+    b = np.zeros(p.N, complex)
+    b[j], b[k] = 1.0, 1j
+    assert abs(oc.bilinear(b, b)) == 0.0 and np.linalg.norm(b) > 0
+    r = oc.shifted_cocg(f, b, Z, p.tol)
+    assert r.status == oc.BREAKDOWN and r.iterations == 0
+    assert np.all(r.x == 0)
+    x, it, status, _ = oc.cocg(lambda v: Z[1] * v - f(v), b, p.tol)
+    assert status == oc.BREAKDOWN and it == 1 and np.all(x == 0)
+    # not quasi-null: the usual solution
+    b2 = np.zeros(p.N, complex)
+    b2[j], b2[k] = 1.0, 0.5j
+    r2 = oc.shifted_cocg(f, b2, Z, p.tol)
+    assert r2.status == oc.OK
+    Hd = dense_hamiltonian(p)
+    for i in (0, 3):
+        xd = np.linalg.solve(Z[i] * np.eye(p.N) - Hd, b2)
+        assert np.linalg.norm(r2.x[i] - xd) <= 1e-8 * np.linalg.norm(xd)
