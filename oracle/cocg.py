@@ -31,6 +31,15 @@ Readings where the paper is silent or at odds with itself:
 6. After a switch the seed's residual vectors are rescaled by the collinear
    factors r^(s~) = r / pi^(s,s~), the seed's alpha_{n-1} and beta_{n-1} are
    taken from alpha_{n-1}^(s~), beta_{n-1}^(s~), and A becomes Z_s~ - H.
+7. Switching to an energy outside the set (the extension the Appendix
+   mentions after Eq. seedswitch): such an auxiliary energy is carried as a
+   shift of its own through Eqs. spi, salpha, sbeta only (pi_{n-1}, pi_n,
+   alpha^(a), beta^(a); no x or p, since nothing of its solution is wanted),
+   so Eq. seedswitch applies to it unchanged.  It can be the first seed and it
+   is a switch candidate like an unconverged energy of the set (largest
+   residual wins; energies of the set come first on ties).  The iteration
+   stops when every energy of the set has converged, whatever the auxiliary
+   shifts' residuals.
 """
 
 from __future__ import annotations
@@ -101,34 +110,44 @@ class ShiftedResult:
     final_res: np.ndarray = None                     # [K] ||r^(i)|| / ||b|| at convergence
 
 
-def shifted_cocg(apply_H, b, Z, tol, rows=None, seed="mid", maxit=100000):
+def shifted_cocg(apply_H, b, Z, tol, rows=None, seed="mid", maxit=100000, aux=None):
     """Solve (Z_i - H) x^(i) = b for every complex energy Z_i (Appendix, Eqs. collinear ... seedswitch).
 
     apply_H(v) returns H v for the real-symmetric H_T.  The seed system is
     A x = b with A = Z_s - H; the shifts are sigma_i = Z_i - Z_s so that
     A + sigma_i I = Z_i - H (Sec. III B).  Only the entries of x^(i), p^(i)
     at ``rows`` are kept (the paper keeps only the required elements).
+
+    ``aux`` (optional) lists complex energies outside the set that may serve
+    as seeds (reading 7); ``seed=("aux", j)`` starts from aux[j].  Seeds in
+    ``seeds`` index the set first, then the auxiliary energies (K + j).
     """
     b = np.asarray(b, dtype=np.complex128)
     Z = np.asarray(Z, dtype=np.complex128)
     K = Z.shape[0]
+    aux = np.zeros(0, np.complex128) if aux is None else np.asarray(aux, dtype=np.complex128).ravel()
     rows = np.arange(b.shape[0]) if rows is None else np.asarray(rows)
     bnorm = np.linalg.norm(b)
     if seed == "mid":
         s = K // 2
     elif seed == "first":
         s = 0
+    elif isinstance(seed, tuple) and seed[0] == "aux":
+        s = K + int(seed[1])
     else:
         s = int(seed)
+    Zset = Z
+    Z = np.concatenate([Zset, aux])          # every shift the scalar recurrences carry
+    KA = Z.shape[0]
 
-    x = np.zeros((K, rows.size), np.complex128)      # x_n^(i) at rows   (x_0 = 0)
+    x = np.zeros((K, rows.size), np.complex128)      # x_n^(i) at rows   (x_0 = 0), set energies only
     p = np.zeros((K, rows.size), np.complex128)      # p_{n-1}^(i) at rows  (p_{-1} = 0)
-    pi_nm1 = np.ones(K, np.complex128)               # pi_{n-1}^(s,i)   (pi_{-1} = 1)
-    pi_n = np.ones(K, np.complex128)                 # pi_n^(s,i)       (pi_0 = 1)
-    alpha_i_nm1 = np.ones(K, np.complex128)          # alpha_{n-1}^(i)  (alpha_{-1} = 1)
-    active = np.ones(K, bool)
-    converged_at = np.full(K, -1)
-    final_res = np.full(K, np.nan)
+    pi_nm1 = np.ones(KA, np.complex128)              # pi_{n-1}^(s,i)   (pi_{-1} = 1)
+    pi_n = np.ones(KA, np.complex128)                # pi_n^(s,i)       (pi_0 = 1)
+    alpha_i_nm1 = np.ones(KA, np.complex128)         # alpha_{n-1}^(i)  (alpha_{-1} = 1)
+    active = np.ones(KA, bool)
+    converged_at = np.full(KA, -1)
+    final_res = np.full(KA, np.nan)
 
     r_nm1 = b.copy()                                 # r_{n-1}  (r_{-1} = b)
     r_n = b.copy()                                   # r_n      (r_0 = b)
@@ -142,6 +161,9 @@ def shifted_cocg(apply_H, b, Z, tol, rows=None, seed="mid", maxit=100000):
     if bnorm == 0.0:
         return ShiftedResult(x, 0, 0, OK, seeds, np.zeros(K, int), np.zeros(K))
 
+    def done(status):
+        return ShiftedResult(x, n, switches, status, seeds, converged_at[:K], final_res[:K])
+
     while True:
         # --- convergence test for r_n^(i) = r_n / pi_n^(s,i)  (reading 2, 3)
         rnorm = np.linalg.norm(r_n)
@@ -150,11 +172,11 @@ def shifted_cocg(apply_H, b, Z, tol, rows=None, seed="mid", maxit=100000):
         converged_at[newly] = n
         final_res[newly] = res[newly]
         active &= ~newly
-        if not active.any():
-            return ShiftedResult(x, n, switches, OK, seeds, converged_at, final_res)
+        if not active[:K].any():
+            return done(OK)
         if n >= maxit:
             final_res[active] = res[active]
-            return ShiftedResult(x, n, switches, MAXIT, seeds, converged_at, final_res)
+            return done(MAXIT)
 
         # --- seed switching (Eq. seedswitch; reading 4, 6)
         if not active[s]:
@@ -181,18 +203,21 @@ def shifted_cocg(apply_H, b, Z, tol, rows=None, seed="mid", maxit=100000):
         rAr = bilinear(r_n, Ar)
         if abs(rr_n) <= 1e-300 or abs(rr_n) <= 1e-28 * rnorm ** 2:
             final_res[active] = res[active]
-            return ShiftedResult(x, n, switches, BREAKDOWN, seeds, converged_at, final_res)
+            return done(BREAKDOWN)
         # Eq. alpha (index shifted by one): alpha_n
         alpha_n = rr_n / (rAr - beta_nm1 / alpha_nm1 * rr_n)
         c_n = beta_nm1 * alpha_n / alpha_nm1
 
-        # --- shifted systems (Eqs. sbeta, endcollinear, spi, salpha, and the x^(i) update)
+        # --- shifted systems (Eqs. sbeta, endcollinear, spi, salpha, and the x^(i) update); the
+        # auxiliary shifts carry only their scalars (reading 7)
         a = active
         beta_i = (pi_nm1[a] / pi_n[a]) ** 2 * beta_nm1                       # beta_{n-1}^(i)
-        p[a] = r_n[rows][None, :] / pi_n[a][:, None] + beta_i[:, None] * p[a]  # p_n^(i)
         pi_np1 = (1.0 + c_n + alpha_n * sigma[a]) * pi_n[a] - c_n * pi_nm1[a]  # pi_{n+1}
         alpha_i = pi_n[a] / pi_np1 * alpha_n                                 # alpha_n^(i)
-        x[a] = x[a] + alpha_i[:, None] * p[a]                                # x_{n+1}^(i)
+        ak = a[:K]
+        nk = int(ak.sum())                                                   # set energies come first in a
+        p[ak] = r_n[rows][None, :] / pi_n[:K][ak][:, None] + beta_i[:nk, None] * p[ak]   # p_n^(i)
+        x[ak] = x[ak] + alpha_i[:nk, None] * p[ak]                           # x_{n+1}^(i)
         alpha_i_nm1[a] = alpha_i
         pi_nm1[a], pi_n[a] = pi_n[a], pi_np1
 

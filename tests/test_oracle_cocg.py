@@ -222,3 +222,34 @@ def test_breakdown_branch_on_a_quasi_null_right_hand_side():
     for i in (0, 3):
         xd = np.linalg.solve(Z[i] * np.eye(p.N) - Hd, b2)
         assert np.linalg.norm(r2.x[i] - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_seed_outside_the_energy_set():
+    """Seed switching to an energy outside the set (the extension stated after Eq. seedswitch): an
+    auxiliary energy carried only through Eqs. spi, salpha, sbeta.  Starting from it, and switching to
+    it, must give the same x^(i) as an in-set seed and as the dense solves, to within the tolerance."""
+    p = small_problem(grid=(6, 5, 8), h=0.5, fd_order=4, n_wells=2, n_energies=5, e_range=(-3.0, -1.0),
+                      eta=5e-2, tol=1e-11)
+    H, P, wE = hamiltonian(p)
+    Z = p.energies + 1j * p.eta
+    f = lambda v: apply_h(H, P, wE, v)
+    rows = boundary_rows(p.grid, p.n_face)
+    b = np.zeros(p.N, complex)
+    b[int(p.cols[1])] = 1.0
+    Hd = dense_hamiltonian(p)
+    xd = np.stack([np.linalg.solve(z * np.eye(p.N) - Hd, b)[rows] for z in Z])
+    ref = oc.shifted_cocg(f, b, Z, p.tol, rows=rows)
+    # 1) the first seed is an energy outside the set, far below the spectrum: it converges first and
+    #    the seed moves into the set
+    z_far = -12.0 + 5e-2j
+    r1 = oc.shifted_cocg(f, b, Z, p.tol, rows=rows, seed=("aux", 0), aux=[z_far])
+    assert r1.status == oc.OK and r1.seeds[0] == p.K and r1.switches >= 1 and r1.seeds[1] < p.K
+    z_in = 1.7 + 3e-2j
+    # 2) the set energies lie below the spectrum (fast); the auxiliary one inside it (slow) has the
+    #    largest residual when the first seed converges, so the switch goes to it
+    r2 = oc.shifted_cocg(f, b, Z, p.tol, rows=rows, seed="first", aux=[z_in])
+    assert r2.status == oc.OK and p.K in r2.seeds[1:]
+    for r in (r1, r2):
+        assert np.linalg.norm(r.x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+        assert np.linalg.norm(r.x - xd) <= 1e-9 * np.linalg.norm(xd)
+        assert r.x.shape == ref.x.shape and r.converged_at.shape == (p.K,)
