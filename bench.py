@@ -237,12 +237,13 @@ def run_gpu(args):
     vsz = 8 if prec == rs.RSFD_MIXED else 16
     h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, proj=p.proj, precision=prec)
     rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, tile_y=args.tile_y,
-                              z_chunk=args.z_chunk, profile=1)
+                              z_chunk=args.z_chunk, pass_kind=args.pass_kind, prefetch=args.prefetch, profile=1)
     tuned = None
     if not args.no_autotune:
         # launch options picked by the library's autotuner for this block width (not timed)
         topts, tus = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(cols.size), iters=256)
         tuned = {"pass_kind": topts["pass_kind"], "tile_y": topts["tile_y"], "rows_per_thread": topts["rows_per_thread"],
+                 "prefetch": topts["prefetch"],
                  "z_chunk": topts["z_chunk"], "iters_per_sync": topts["iters_per_sync"],
                  "reg_budget": topts["reg_budget"], "tile_x": topts["tile_x"], "us_per_slot_iteration": tus}
     G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
@@ -267,7 +268,7 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     agg = {"ms_pass": 0.0, "ms_shift": 0.0, "slot_iterations": 0, "shift_updates": 0, "shift_slot_chunks": 0,
-           "n_pass": 0, "n_shift": 0, "n_other": 0}
+           "n_pass": 0, "n_shift": 0, "n_other": 0, "ms_combine": 0.0}
     statuses, iters = [], []
     for _ in range(args.steps):
         st, info = step()
@@ -289,13 +290,38 @@ def run_gpu(args):
     # roofline of the dominant kernel (algorithmic bytes / summed event-timed duration)
     N, nb, K = p.N, h.nb, p.K
     # fused pass: read r_{n-1}, r_{n-2}, write r_n per slot-iteration, plus V once per launch
-    pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + agg["n_pass"] * (vsz // 2) * N
+    kind_used = tuned["pass_kind"] if tuned else args.pass_kind
+    launches_per_iter = 2 if kind_used == 3 else 1        # the split pass: combine + stencil launches
+    iter_launches = agg["n_pass"] / launches_per_iter     # seed iterations launched (all slots at once)
+    pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + iter_launches * (vsz // 2) * N
+    proj_bytes_per_it = 0
+    if p.proj is not None:
+        # separable projectors (timed with the pass): the gather c_a = h^3 p_a^T r reads r, the value and
+        # the index of every entry; the scatter reads and writes A r on the union of the supports and
+        # reads every entry's value and atom index
+        nnz = int(p.proj.nnz)
+        n_supp = int(np.unique(p.proj.idx).size)
+        s_p = vsz // 2
+        proj_bytes_per_it = nnz * (vsz + s_p + 8) + n_supp * 2 * vsz + nnz * (s_p + 4)
+        pass_bytes += agg["slot_iterations"] * proj_bytes_per_it
     # collapsed shift update: read and write x_b, p_b of K energies once per (slot, collapse) and read
     # the recorded boundary rows of the residuals once
     hsz = 16 if prec == rs.RSFD_FP64 else 8
     shift_bytes = agg["shift_slot_chunks"] * K * 4 * vsz * nb + agg["slot_iterations"] * hsz * nb
     peak, peak_src = _peaks()
     kern = {"pass": (pass_bytes, agg["ms_pass"]), "shift": (shift_bytes, agg["ms_shift"])}
+    split = None
+    if kind_used == 3 and agg["ms_combine"] > 0:
+        # the split pass's two launches against their own algorithmic bytes: the combine reads r_{n-1},
+        # r_{n-2}, A r_{n-1} and writes r_n (4 v N); the stencil reads r_n and writes A r_n (2 v N, plus
+        # the potential once per launch and the projector terms)
+        cb = agg["slot_iterations"] * 4 * vsz * N
+        sb = pass_bytes - agg["slot_iterations"] * 3 * vsz * N + agg["slot_iterations"] * 2 * vsz * N
+        cms, sms = agg["ms_combine"], agg["ms_pass"] - agg["ms_combine"]
+        split = {"combine": {"alg_bytes": cb, "ms": cms, "GBps": cb / (cms / 1e3) / 1e9,
+                             "frac": cb / (cms / 1e3) / 1e9 / _peaks()[0]},
+                 "stencil": {"alg_bytes": sb, "ms": sms, "GBps": sb / (sms / 1e3) / 1e9,
+                             "frac": sb / (sms / 1e3) / 1e9 / _peaks()[0]}}
     dom = max(kern, key=lambda k: kern[k][1])
     dbytes, dms = kern[dom]
     achieved = dbytes / (dms / 1e3) / 1e9 if dms > 0 else None
@@ -308,8 +334,9 @@ def run_gpu(args):
             t = json.load(open(tfile)).get(dom)
             lo = tuned or {"tile_y": args.tile_y, "z_chunk": args.z_chunk}
             if (t and t.get("workload") == p.name and t.get("precision") == p.precision
-                    and t.get("tile_y") == lo.get("tile_y") and t.get("z_chunk") == lo.get("z_chunk")):
-                traffic = t["bytes_per_slot_iteration"] * agg["slot_iterations"] / agg["n_pass"]
+                    and t.get("tile_y") == lo.get("tile_y") and t.get("z_chunk") == lo.get("z_chunk")
+                    and t.get("pass_kind", 2) == (kind_used or 2)):
+                traffic = t["bytes_per_slot_iteration"] * agg["slot_iterations"] / iter_launches
         except Exception:
             traffic = None
 
@@ -360,11 +387,13 @@ def run_gpu(args):
                    "launch_options": tuned if tuned else "defaults"},
         "status": [int(x) for x in statuses], "mean_iterations_per_column": statistics.mean(iters),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "alg_bytes_per_slot_iteration": 3 * vsz * N + proj_bytes_per_it,
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": peak_src,
                      "kernels": {k: {"alg_bytes": v[0], "ms": v[1],
                                      "GBps": (v[0] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None}
-                                 for k, v in kern.items()}},
+                                 for k, v in kern.items()},
+                     "split_launches": split},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
@@ -452,35 +481,51 @@ def run_shift_scaling(args):
     h.close()
 
 
+def _golden(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_golden.npz")
+    return np.load(path) if os.path.exists(path) else None
+
+
 def run_precision_speedup(args):
-    """Reduced-precision forms against the plain FP64 GPU form on the full pipeline (G0_bb for every
-    boundary column, Dyson, T), where the transmission can be compared: a 16x16x48 grid (h = 0.4,
-    4th order, 6 wells, two boundary planes per side), 16 energies in [0.3, 1.0] Ha, eta = 1e-3 and
-    1e-2.  Every form runs at the same stopping tolerance (1e-6); accuracy is measured against an FP64
-    run at tol 1e-10, and the speedup over the FP64 form at tol 1e-6 is reported where |dT| <= 1e-4
-    and the G_bb error <= 1e-5 hold.  One JSON line per (eta, precision)."""
+    """Reduced-precision forms against the plain FP64 GPU form, with errors taken against stored
+    oracle values (tests/golden, written by tests/golden/make_golden.py, which calls only the oracle).
+
+    * tiny_wire_fp64 (8x8x12, 2nd order, 3 wells, all 128 plane columns, 8 energies, eta = 1e-3): the
+      full pipeline per form -- shifted COCG of every boundary column, Dyson with the closed-form lead
+      self-energies, T -- every form stopped at tol 1e-6 (and the FP64 form also at the configuration's
+      1e-12); G_bb and T errors against the oracle's dense (Z - H - Sigma)^{-1} and its T.
+    * sampled_columns_mixed (64x64x128, 4th order, 128 energies, eta = 1e-3): the bench's first block of
+      --cols-per-step columns solved by each form at tol 1e-8 (at the workload's 1e-6 every form, FP64
+      included, stops about 1e-4 from the converged G0_bb, since the error is about tol / eta); G0_bb
+      error on the stored oracle rows of the stored columns (oracle at tol 1e-10).  complex64 vectors stall near eps_32 * kappa here, so that
+      form is capped at 40 000 iterations and reported as not converged.
+    One JSON line per (workload, form); speedup_vs_fp64 is given where the form meets the mixed-mode
+    tolerances (G_bb or G0_bb error <= 1e-5, |dT| <= 1e-4)."""
     import torch
     import paper_1502_00081_gb300 as rs
-    from workloads import small_problem
+    from workloads import make_problem
     torch.cuda.set_device(0)
     rs.load_library()
-    tol = 1e-6
-    for eta in (1e-3, 1e-2):
-        p = small_problem(grid=(16, 16, 48), h=0.4, fd_order=4, n_wells=6, n_energies=16, e_range=(0.3, 1.0),
-                          eta=eta, tol=tol, n_face=2, seed=17)
-        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+    forms = (("fp64", rs.RSFD_FP64), ("df64", rs.RSFD_DF64), ("mixed", rs.RSFD_MIXED))
 
-        def run(prec, tol_run, maxit, reps):
-            with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=2, precision=prec) as h:
+    g1 = _golden("tiny_wire_fp64")
+    if g1 is not None:
+        p = make_problem("tiny_wire_fp64")
+        SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
+        Go, To = g1["G_bb"], g1["T"]
+
+        def run1(prec, tol_run, reps=3):
+            with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec) as h:
+                assert np.array_equal(np.asarray(h.rows), g1["rows"])
                 cols = np.asarray(h.rows)
                 G0 = torch.zeros((p.K, cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
                 SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
                 G = torch.empty_like(G0)
                 best = None
-                for rep in range(reps):
+                for _ in range(reps):
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, tol_run, maxit, G0)
+                    st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, tol_run, 200000, G0)
                     torch.cuda.synchronize()
                     t1 = time.perf_counter()
                     rs.rsfd_dyson_boundary(h.ptr, G0, SL, SR, G)
@@ -488,23 +533,128 @@ def run_precision_speedup(args):
                     torch.cuda.synchronize()
                     t = (time.perf_counter() - t0, t1 - t0)
                     best = t if best is None or t[0] < best[0] else best
-                return best, int(st), float(info["iters"].mean()), np.asarray(T), G.cpu().numpy().astype(np.complex128)
+                Gm = G.cpu().numpy().astype(np.complex128).transpose(0, 2, 1)
+                return best, int(st), float(info["iters"].mean()), np.asarray(T), Gm
 
-        _, _, _, T_ref, G_ref = run(rs.RSFD_FP64, 1e-10, 200000, 1)
         base = None
-        for name, prec in (("fp64", rs.RSFD_FP64), ("df64", rs.RSFD_DF64), ("mixed", rs.RSFD_MIXED)):
-            (tot, cocg), st, its, T, G = run(prec, tol, 20000, 2)
-            dT = float(np.abs(T - T_ref).max())
-            gerr = float(np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref))
-            ok = st == 0 and dT <= 1e-4 and gerr <= 1e-5
+        for name, prec in forms:
+            for tol_run in ((1e-6, 1e-12) if name == "fp64" else (1e-6,)):
+                (tot, cocg), st, its, T, G = run1(prec, tol_run)
+                dT = float(np.abs(T - To).max())
+                gerr = float(max(np.linalg.norm(G[k] - Go[k]) / np.linalg.norm(Go[k]) for k in range(p.K)))
+                ok = st == 0 and dT <= 1e-4 and gerr <= 1e-5
+                if name == "fp64" and tol_run == 1e-6:
+                    base = tot
+                print(json.dumps({"experiment": "precision_speedup", "workload": p.name, "precision": name,
+                                  "tol": tol_run, "status": st, "seconds": tot, "cocg_seconds": cocg,
+                                  "columns": int(G.shape[2]), "energies": p.K, "mean_seed_iterations": its,
+                                  "max_abs_dT": dT, "G_bb_rel_err_max": gerr,
+                                  "reference": "oracle dense (Z - H - Sigma)^-1 and T (tests/golden)",
+                                  "meets_tolerances": ok,
+                                  "speedup_vs_fp64": (base / tot) if ok and base and tol_run == 1e-6 else None}),
+                      flush=True)
+
+    g2 = _golden("sampled_columns_mixed")
+    if g2 is not None:
+        p = make_problem("sampled_columns_mixed")
+        B = args.cols_per_step if args.cols_per_step > 0 else 38
+        batch = p.cols[:B]
+        gcols, rows, Gref = g2["cols"], g2["rows"], g2["G0"]
+        pos = [int(np.where(batch == c)[0][0]) for c in gcols]
+        base = None
+        for name, prec in forms:
+            with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec) as h:
+                rs.rsfd_set_solve_options(h.ptr, profile=1)
+                if prec != rs.RSFD_FP64:
+                    rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(batch.size), iters=256)
+                else:
+                    rs.rsfd_set_solve_options(h.ptr, slots=int(batch.size), profile=1)
+                ridx = np.searchsorted(np.asarray(h.rows), rows)
+                G0 = torch.zeros((p.K, batch.size, h.nb), dtype=h.complex_dtype, device="cuda")
+                maxit = 40000 if prec == rs.RSFD_MIXED else 4 * p.maxit
+                tol2 = 1e-8
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, info, res = rs.rsfd_shifted_cocg(h.ptr, batch, p.energies, p.eta, tol2, maxit, G0)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                G = G0.cpu().numpy()
+            Gs = np.stack([G[:, j, :][:, ridx] for j in pos], axis=-1).astype(np.complex128)
+            gerr = float(np.linalg.norm(Gs - Gref) / np.linalg.norm(Gref))
+            ok = st == 0 and gerr <= 1e-5
             if name == "fp64":
-                base = tot
-            print(json.dumps({"experiment": "precision_speedup", "eta": eta, "precision": name, "tol": tol,
-                              "status": st, "seconds": tot, "cocg_seconds": cocg, "columns": int(G.shape[1]),
-                              "energies": p.K, "mean_seed_iterations": its, "max_abs_dT": dT,
-                              "G_bb_rel_err": gerr, "reference": "FP64 GPU form at tol 1e-10",
+                base = dt
+            print(json.dumps({"experiment": "precision_speedup", "workload": p.name, "precision": name,
+                              "tol": tol2, "status": int(st), "cocg_seconds": dt, "columns": int(batch.size),
+                              "energies": p.K, "mean_seed_iterations": float(info["iters"].mean()),
+                              "G0_bb_rel_err": gerr,
+                              "reference": "oracle G0_bb at tol 1e-10 on the stored rows and columns (tests/golden)",
                               "meets_tolerances": ok,
-                              "speedup_vs_fp64": (base / tot) if ok and base else None}), flush=True)
+                              "speedup_vs_fp64": (base / dt) if ok and base else None}), flush=True)
+
+
+def run_full_boundary(args):
+    """The full-boundary workload end to end on one GPU: 48x48x160 grid, h = 0.4, 4th order, 140 seeded
+    wells, every one of the 2 x 2 x 48 x 48 = 9216 boundary-slab columns, 64 energies in [-0.5, 0.5]
+    Ha at eta = 5e-4, tolerance 1e-6, double-float vectors.  Phases: the shifted COCG of all columns
+    into a device G0_bb [64][9216][9216] (complex128, 87 GB), then, in energy chunks, the lead
+    self-energies (closed form), the Dyson step (tensor-core LU, FP64 refinement of the left slab's
+    columns, the block the transmission reads) and T(E).  One JSON line with the seconds per phase,
+    the COCG throughput and T(E)."""
+    import torch
+    import paper_1502_00081_gb300 as rs
+    from workloads import make_problem
+    torch.cuda.set_device(0)
+    rs.load_library()
+    p = make_problem("full_boundary")
+    if args.ncols:
+        p.cols = p.cols[:args.ncols]
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_DF64) as h:
+        cols = np.asarray(h.rows) if not args.ncols else np.asarray(h.rows)[:args.ncols]
+        nb = h.nb
+        rs.rsfd_set_solve_options(h.ptr, profile=1)
+        topts, tus = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=min(256, cols.size), iters=256)
+        G0 = torch.zeros((p.K, cols.size, nb), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, cols, p.energies, p.eta, p.tol, 4 * p.maxit, G0)
+        torch.cuda.synchronize()
+        t_cocg = time.perf_counter() - t0
+        stats = rs.rsfd_get_stats(h.ptr)
+        T_all, t_sigma, t_dyson, t_T, refres = [], 0.0, 0.0, 0.0, []
+        if cols.size == nb:
+            rs.rsfd_set_solve_options(h.ptr, dyson_cols=1, **{k: topts[k] for k in ("pass_kind", "tile_y", "z_chunk")})
+            kc = 16
+            for k0 in range(0, p.K, kc):
+                E = p.energies[k0:k0 + kc]
+                ta = time.perf_counter()
+                SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, E, p.eta)
+                SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
+                torch.cuda.synchronize()
+                tb = time.perf_counter()
+                G = torch.empty((E.size, nb, nb), dtype=torch.complex128, device="cuda")
+                refres += list(rs.rsfd_dyson_boundary(h.ptr, G0[k0:k0 + kc], SL, SR, G))
+                torch.cuda.synchronize()
+                tc = time.perf_counter()
+                T_all += list(rs.rsfd_transmission(h.ptr, G, SL, SR))
+                torch.cuda.synchronize()
+                td = time.perf_counter()
+                t_sigma += tb - ta
+                t_dyson += tc - tb
+                t_T += td - tc
+                del G, SL, SR
+    print(json.dumps({"experiment": "full_boundary", "workload": p.name, "grid": list(p.grid), "columns": int(cols.size),
+                      "boundary_rows": int(nb), "energies": p.K, "eta": p.eta, "tol": p.tol, "precision": "df64",
+                      "launch_options": {k: topts[k] for k in ("pass_kind", "tile_y", "z_chunk", "prefetch")},
+                      "status": int(st), "columns_not_ok": int((info["status"] != 0).sum()),
+                      "mean_seed_iterations": float(info["iters"].mean()),
+                      "cocg_seconds": t_cocg, "cocg_columns_x_energies_per_s": cols.size * p.K / t_cocg,
+                      "pass_ms": stats["ms_pass"], "shift_ms": stats["ms_shift"],
+                      "sigma_seconds": t_sigma, "dyson_seconds": t_dyson, "transmission_seconds": t_T,
+                      "dyson_form": "tensor-core LU (3xTF32), FP64 refinement, left-slab columns",
+                      "dyson_refine_residual_max": float(max(refres)) if refres else None,
+                      "T": [float(t) for t in T_all],
+                      "T_nonnegative": bool(all(t >= -1e-6 for t in T_all)) if T_all else None}), flush=True)
 
 
 def run_dyson_scaling(args):
@@ -653,6 +803,9 @@ def main():
                          "exactly four waves of the 152 SMs x 2 resident CTAs")
     ap.add_argument("--maxit", type=int, default=0, help="iteration cap per column (profiling runs)")
     ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--prefetch", type=int, default=0, help="with --no-autotune: TMA planes in flight (1..7)")
+    ap.add_argument("--pass-kind", type=int, default=0,
+                    help="with --no-autotune: 1 fused, 2 stored-product, 3 split (combine + stencil launches)")
     ap.add_argument("--z-chunk", type=int, default=0)
     ap.add_argument("--ncols", type=int, default=0, help="use only the first n columns (quick runs)")
     ap.add_argument("--slots", type=int, default=0)
@@ -664,7 +817,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--experiment", default=None,
                     choices=[None, "shift_scaling", "precision_speedup", "dyson_scaling", "tc_gemm",
-                             "uneven_regions"],
+                             "uneven_regions", "full_boundary"],
                     help="run an experiment instead of the benchmark (JSON lines)")
     ap.add_argument("--dyson-max-nb", type=int, default=0, help="dyson_scaling: largest boundary size (0 = all)")
     ap.add_argument("--gemm-size", type=int, default=0, help="tc_gemm: only the shapes with this m (0 = all)")
@@ -685,6 +838,9 @@ def main():
         return
     if args.experiment == "uneven_regions":
         run_uneven_regions(args)
+        return
+    if args.experiment == "full_boundary":
+        run_full_boundary(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -84,7 +84,8 @@ typedef enum { RSFD_FP64 = 0, RSFD_MIXED = 1, RSFD_DF64 = 2 } rsfd_precision;
 typedef enum {
   RSFD_SEED_MID = 0,   /* energy index K/2 */
   RSFD_SEED_FIRST = 1, /* energy index 0 */
-  RSFD_SEED_INDEX = 2  /* energy index seed_index */
+  RSFD_SEED_INDEX = 2, /* energy index seed_index */
+  RSFD_SEED_AUX = 3    /* auxiliary energy seed_index of rsfd_shifted_cocg_aux (outside the set) */
 } rsfd_seed_kind;
 
 /* Separable nonlocal projectors, one per atom (Sec. II A mentions nonlocal
@@ -111,8 +112,11 @@ typedef enum {
   RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED (measured faster in every precision on the 64^2 x 128 workload) */
   RSFD_PASS_RECOMPUTE = 1, /* three vectors per iteration (r_{n-1}, r_{n-2} in, r_n out); A r_{n-1} is
                               recomputed on the tile plus halo and A r_n again for the dot products */
-  RSFD_PASS_STORED = 2     /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);
+  RSFD_PASS_STORED = 2,    /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);
                               one stencil application per grid point */
+  RSFD_PASS_SPLIT = 3      /* the stored-product iteration as two launches: a pointwise combine (r_n from
+                              r_{n-1}, r_{n-2}, A r_{n-1}; four vectors) and a stencil (A r_n from r_n; two
+                              vectors plus its halo); one row per thread, tile width 32, tile_y <= 16 */
 } rsfd_pass_kind;
 
 /* Form of the Dyson solve (rsfd_solve_opts.dyson_kind). */
@@ -151,6 +155,9 @@ typedef struct {
                              declared lost (each attempt sleeps up to 1 ms): 0 = 4096; -1 = none, so every
                              CTA's first wait expires at once (a test of the RSFD_ERR_TIMEOUT path: the CTA
                              still drains its issued transfers with the full cap before it returns) */
+  int32_t dyson_cols;     /* columns of G_bb rsfd_dyson_boundary solves: 0 = all nb; 1 = the left slab's nb/2
+                             only (solve, refinement and residual on half the right-hand sides), the
+                             block rsfd_transmission reads (G_RL); the other columns are set to zero */
   double breakdown_tol;   /* quasi-null test of the seed's (r_n, r_n): breakdown when |(r,r)| <= this times
                              ||r||^2 (or <= 1e-300); 0 = 1e-28.  A large value makes every column report
                              RSFD_ERR_BREAKDOWN (a test of that path) */
@@ -161,7 +168,7 @@ typedef struct {
   double ms_total;            /* wall time of the call on the device stream (events) */
   double ms_pass;             /* summed duration of stencil/seed-update launches (profile = 1) */
   double ms_shift;            /* summed duration of the collapsed shift-update launches (profile = 1) */
-  int64_t n_pass;             /* stencil/seed-update launches */
+  int64_t n_pass;             /* stencil/seed-update launches (two per iteration for RSFD_PASS_SPLIT) */
   int64_t n_shift;            /* collapsed shift-update launches (the apply kernel) */
   int64_t n_other;            /* other kernel launches (collapse coefficients, history reset, projector
                                  terms, slot set-up, write-out) */
@@ -170,6 +177,7 @@ typedef struct {
   int64_t shift_slot_chunks;  /* (column, collapse) pairs: each reads and writes x_b, p_b of K energies once */
   int32_t slots;              /* columns in flight that were used */
   int32_t iters_per_sync;
+  double ms_combine;          /* RSFD_PASS_SPLIT with profile = 1: the combine launches' part of ms_pass */
 } rsfd_stats;
 
 /* Create a handle for one transition region (Sec. II A, Eq. sabun1).
@@ -228,6 +236,21 @@ rsfd_status rsfd_set_solve_options(rsfd_handle h, const rsfd_solve_opts* opts);
 rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
                               double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
                               void* G0_bb, rsfd_col_info* info, double* final_res);
+
+/* Shifted COCG with seed switching to energies outside the set (Appendix: the extension of Eq.
+ * seedswitch to an arbitrary energy point, which the paper cites from its Ref. ss).  As
+ * rsfd_shifted_cocg, plus n_aux auxiliary energies (host [n_aux], Z_a = aux_energies[a] + i*eta)
+ * that are carried as shifts of their own through the scalar recurrences (Eqs. spi, salpha,
+ * sbeta) so that Eq. seedswitch applies to them unchanged: one of them can be the first seed
+ * (seed_kind RSFD_SEED_AUX, seed_index < n_aux), and at every seed switch they are candidates
+ * like the unconverged energies of the set (largest residual wins; the set comes first on ties).
+ * Nothing of their solutions is output and a column stops when the K energies of the set have
+ * converged.  G0_bb, info and final_res cover the K energies only; info.final_seed >= K names
+ * auxiliary energy final_seed - K.  n_aux = 0 is rsfd_shifted_cocg. */
+rsfd_status rsfd_shifted_cocg_aux(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+                                  const double* aux_energies, int32_t n_aux, double eta, double tol, int32_t maxit,
+                                  int32_t seed_kind, int32_t seed_index, void* G0_bb, rsfd_col_info* info,
+                                  double* final_res);
 
 /* Launch-option autotuner for rsfd_shifted_cocg (the seed iteration and shift update of Sec. III B and
  * the Appendix; the paper has no launch shapes, so the tuned quantities are this library's own):

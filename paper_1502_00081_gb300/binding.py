@@ -27,9 +27,11 @@ RSFD_DF64 = 2
 RSFD_SEED_MID = 0
 RSFD_SEED_FIRST = 1
 RSFD_SEED_INDEX = 2
+RSFD_SEED_AUX = 3
 RSFD_PASS_AUTO = 0
 RSFD_PASS_RECOMPUTE = 1
 RSFD_PASS_STORED = 2
+RSFD_PASS_SPLIT = 3
 RSFD_DYSON_AUTO = 0
 RSFD_DYSON_FP64 = 1
 RSFD_DYSON_TC = 2
@@ -60,7 +62,8 @@ class rsfd_solve_opts(ctypes.Structure):
                 ("z_chunk", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("pass_kind", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
                 ("dyson_kind", ctypes.c_int32), ("dyson_refine", ctypes.c_int32), ("reg_budget", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("wait_cap", ctypes.c_int32), ("breakdown_tol", ctypes.c_double)]
+                ("tile_x", ctypes.c_int32), ("wait_cap", ctypes.c_int32), ("dyson_cols", ctypes.c_int32),
+                ("breakdown_tol", ctypes.c_double)]
 
 
 class rsfd_region_solve(ctypes.Structure):
@@ -77,7 +80,7 @@ class rsfd_stats(ctypes.Structure):
                 ("n_pass", ctypes.c_int64), ("n_shift", ctypes.c_int64), ("n_other", ctypes.c_int64),
                 ("slot_iterations", ctypes.c_int64), ("shift_updates", ctypes.c_int64),
                 ("shift_slot_chunks", ctypes.c_int64),
-                ("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32)]
+                ("slots", ctypes.c_int32), ("iters_per_sync", ctypes.c_int32), ("ms_combine", ctypes.c_double)]
 
 
 # every symbol declared in include/rsfd.h, with (restype, argtypes)
@@ -94,6 +97,11 @@ _SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                          ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
+    "rsfd_shifted_cocg_aux": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                             ctypes.POINTER(rsfd_col_info), ctypes.POINTER(ctypes.c_double)]),
     "rsfd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(rsfd_stats)]),
     "rsfd_lead_sigma_decimation": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
@@ -253,16 +261,18 @@ def rsfd_boundary_rows(h):
 
 def rsfd_set_solve_options(h, slots=0, iters_per_sync=0, tile_y=0, z_chunk=0, use_graphs=0, profile=0,
                            pass_kind=0, prefetch=0, rows_per_thread=0, dyson_kind=0, dyson_refine=0, reg_budget=0,
-                           tile_x=0, wait_cap=0, breakdown_tol=0.0):
+                           tile_x=0, wait_cap=0, dyson_cols=0, breakdown_tol=0.0):
     lib = load_library()
     o = rsfd_solve_opts(int(slots), int(iters_per_sync), int(tile_y), int(z_chunk), int(use_graphs), int(profile),
                         int(pass_kind), int(prefetch), int(rows_per_thread), int(dyson_kind), int(dyson_refine),
-                        int(reg_budget), int(tile_x), int(wait_cap), float(breakdown_tol))
+                        int(reg_budget), int(tile_x), int(wait_cap), int(dyson_cols), float(breakdown_tol))
     _check(h, lib.rsfd_set_solve_options(h, ctypes.byref(o)))
 
 
-def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_SEED_MID, seed_index=0):
-    """Returns (status, info [ncols] structured array, final_res [ncols, K])."""
+def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_SEED_MID, seed_index=0,
+                      aux_energies=None):
+    """Returns (status, info [ncols] structured array, final_res [ncols, K]).  With aux_energies the
+    call goes to rsfd_shifted_cocg_aux (seed candidates outside the set)."""
     import torch
     lib = load_library()
     c, cp = _i64(cols)
@@ -270,9 +280,15 @@ def rsfd_shifted_cocg(h, cols, energies, eta, tol, maxit, G0_bb, seed_kind=RSFD_
     ptr = _dev_ptr(G0_bb, (torch.complex64, torch.complex128), name="G0_bb")
     info = (rsfd_col_info * c.size)()
     res = np.zeros((c.size, e.size), np.float64)
-    st = lib.rsfd_shifted_cocg(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
-                               int(seed_kind), int(seed_index), ptr, info,
-                               res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if aux_energies is None:
+        st = lib.rsfd_shifted_cocg(h, cp, int(c.size), ep, int(e.size), float(eta), float(tol), int(maxit),
+                                   int(seed_kind), int(seed_index), ptr, info,
+                                   res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    else:
+        a, apt = _f64(aux_energies)
+        st = lib.rsfd_shifted_cocg_aux(h, cp, int(c.size), ep, int(e.size), apt, int(a.size), float(eta), float(tol),
+                                       int(maxit), int(seed_kind), int(seed_index), ptr, info,
+                                       res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     _check(h, st, allow=(RSFD_ERR_NOT_CONVERGED, RSFD_ERR_BREAKDOWN))
     arr = np.array([(i.iters, i.switches, i.status, i.final_seed) for i in info],
                    dtype=[("iters", np.int32), ("switches", np.int32), ("status", np.int32),

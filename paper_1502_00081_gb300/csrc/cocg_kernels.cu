@@ -398,6 +398,16 @@ template <> struct Acc<double> {
     ra_y = fma(r.x, v.y, fma(r.y, v.x, ra_y));
     nn = fma(r.x, r.x, fma(r.y, r.y, nn));
   }
+  // the split pass forms (r,r) and ||r||^2 where r_n is produced and (r,Ar) where A r_n is
+  __device__ __forceinline__ void add_r(double2 r) {
+    rr_x = fma(r.x, r.x, fma(-r.y, r.y, rr_x));
+    rr_y = fma(2.0 * r.x, r.y, rr_y);
+    nn = fma(r.x, r.x, fma(r.y, r.y, nn));
+  }
+  __device__ __forceinline__ void add_ra(double2 r, double2 v) {
+    ra_x = fma(r.x, v.x, fma(-r.y, v.y, ra_x));
+    ra_y = fma(r.x, v.y, fma(r.y, v.x, ra_y));
+  }
   // warp sums (whole warps only); lane 0 returns them, the other lanes zeros
   __device__ __forceinline__ void get(double* o) const {
     double t[5] = {rr_x, rr_y, ra_x, ra_y, nn};
@@ -442,6 +452,19 @@ struct AccDF {
     nn = __fmaf_rn(rh.x, rh.x, __fmaf_rn(rh.y, rh.y, nn));
   }
   __device__ __forceinline__ void add(const dfc& r, const dfc& v) { add2(r.h, r.l, v.h, v.l); }
+  __device__ __forceinline__ void add_r(const dfc& r) {
+    const float2 rh = r.h, rl = r.l;
+    addprod(rr_s, rr_l, bc(rh.x), bc(rl.x), rh, rl);
+    addprod(rr_s, rr_l, make_float2(-rh.y, rh.y), make_float2(-rl.y, rl.y), make_float2(rh.y, rh.x),
+            make_float2(rl.y, rl.x));
+    nn = __fmaf_rn(rh.x, rh.x, __fmaf_rn(rh.y, rh.y, nn));
+  }
+  __device__ __forceinline__ void add_ra(const dfc& r, const dfc& v) {
+    const float2 rh = r.h, rl = r.l;
+    addprod(ra_s, ra_l, bc(rh.x), bc(rl.x), v.h, v.l);
+    addprod(ra_s, ra_l, make_float2(-rh.y, rh.y), make_float2(-rl.y, rl.y), make_float2(v.h.y, v.h.x),
+            make_float2(v.l.y, v.l.x));
+  }
   static __device__ __forceinline__ float2 shfl2(float2 v, int o) {
     return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
   }
@@ -490,6 +513,13 @@ struct AccK {
     kahan(ra, ra_c, tra);
     nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
   }
+  __device__ __forceinline__ void add_r(float2 r) {
+    kahan(rr, rr_c, make_float2(__fmaf_rn(r.x, r.x, -r.y * r.y), 2.f * r.x * r.y));
+    nn = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, nn));
+  }
+  __device__ __forceinline__ void add_ra(float2 r, float2 v) {
+    kahan(ra, ra_c, make_float2(__fmaf_rn(r.x, v.x, -r.y * v.y), __fmaf_rn(r.x, v.y, r.y * v.x)));
+  }
   // The Kahan pairs (s, -c) are double-float values: reduce them over the warp with TwoSum merges
   // (whole warps only) and convert once; lane 0 returns the warp's sums, the other lanes zeros.
   __device__ __forceinline__ void get(double* o) {
@@ -536,6 +566,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Bounded wait for the phase with the given parity; false when the cap is reached (cap attempts).  Each try_wait
 // carries a suspend-time hint, so a waiting thread sleeps until the phase completes (or the hint
@@ -669,7 +702,7 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
       q.active = 0;
       q.conv_iter = n;
     } else {
-      ++cnt;
+      if (i < p.d.kreq) ++cnt;   // auxiliary seed energies do not keep the column running
       if (res > best) { best = res; best_i = i; }
     }
   }
@@ -824,13 +857,14 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
 }
 
 // Per-CTA partial sums (lane 0 of each warp holds its warp's sums) -> the slot's partial array ->
-// atomic ticket; the last CTA of the slot sums the partials in CTA order (warp 0, fixed tree) and
-// returns true with (r,r), (r,Ar), ||r||^2 in S.  No CTA waits on another.
+// atomic ticket; the last of the slot's ctas_per_slot CTAs sums all npart partials of the slot in
+// order (warp 0, fixed tree; the split pass's combine kernel has left its partials in entries
+// ctas_per_slot ...) and returns true with (r,r), (r,Ar), ||r||^2 in S.  No CTA waits on another.
 __device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)[5], ScalarShared& S, int& s_last) {
   const int tid = threadIdx.x;
   block_sum_lane0<5>(v5, S.red);
   if (tid == 0) {
-    double* dst = p.partials + ((size_t)slot * p.d.ctas_per_slot + cta) * 8;
+    double* dst = p.partials + ((size_t)slot * p.d.npart + cta) * 8;
 #pragma unroll
     for (int k = 0; k < 5; ++k) dst[k] = v5[k];
     __threadfence();
@@ -842,8 +876,8 @@ __device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)
   __threadfence();
   if (tid < 32) {
     double w5[5] = {0, 0, 0, 0, 0};
-    const double* src = p.partials + (size_t)slot * p.d.ctas_per_slot * 8;
-    for (int k = tid; k < p.d.ctas_per_slot; k += 32) {
+    const double* src = p.partials + (size_t)slot * p.d.npart * 8;
+    for (int k = tid; k < p.d.npart; k += 32) {
 #pragma unroll
       for (int j = 0; j < 5; ++j) w5[j] += __ldcg(src + (size_t)k * 8 + j);
     }
@@ -1455,6 +1489,339 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
 }
 
 // ------------------------------------------------------------------------------------------------
+// the split pass: a pointwise combine kernel, then a stencil kernel
+// ------------------------------------------------------------------------------------------------
+// The stored-product iteration (five vectors) as two launches per iteration:
+//
+//   combine_kernel:  r_n = a1 r_{n-1} + a2 r_{n-2} + aA u_{n-1}   (pointwise, Eq. rvec), the boundary
+//                    rows of r_n for the shift update, and the partial sums of (r_n, r_n), ||r_n||^2;
+//   stencil_kernel:  u_n = A r_n (one stencil application per point) and the partial sums of
+//                    (r_n, A r_n); the last CTA of a slot reduces both kernels' partials in a fixed
+//                    order and runs the FP64 scalar step.
+//
+// The combine moves four vectors and is bound by HBM bandwidth; the stencil moves two (plus its
+// halo from L2) and carries the stencil's arithmetic without the combine's registers, so neither
+// half limits the other's occupancy.  Per iteration the pair moves six vectors against the stored
+// pass's five, in exchange for every grid point's stencil and combine being computed once (no frame
+// recomputation).
+
+// Combine: CTA = 256 threads over a range of z-planes of one slot; each thread walks the plane's
+// padded elements with stride 256 (x, y tracked by a running counter) and handles two elements per
+// step so that six 16-byte loads are in flight.
+constexpr int kCombThreads = 256;
+
+template <int MODE>
+__global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
+  typedef Ops<MODE> O;
+  typedef Stencil<MODE, 1> ST;   // combine() does not depend on the stencil reach
+  typedef typename O::C C;
+  typedef typename O::H H;
+  __shared__ double s_red[32 * 5];
+  __shared__ typename O::Cplx s_a[3];
+  __shared__ int s_n, s_hc;
+  const int slot = blockIdx.y;
+  const SlotState* st = p.slots + slot;
+  if (st->status != SLOT_RUNNING) return;
+  const SolveDims& d = p.d;
+  if (threadIdx.x == 0) {
+    s_a[0] = O::cplx(st->a1);
+    s_a[1] = O::cplx(st->a2);
+    s_a[2] = O::cplx(st->aA);
+    s_n = st->n;
+    s_hc = st->hcnt;
+  }
+  __syncthreads();
+  const typename O::Cplx a1 = s_a[0], a2 = s_a[1], aA = s_a[2];
+  const int n = s_n;
+  const int i1 = (n + 2) % 3, i2 = (n + 1) % 3, io = n % 3, iu1 = 3 + (n + 1) % 2;
+  const long long pe = (long long)d.nxp * d.ny;   // padded elements per plane
+  const long long vec = (long long)d.nz * pe;
+  const C* R1 = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 5 + i1) * vec;
+  const C* R2 = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 5 + i2) * vec;
+  const C* U1 = reinterpret_cast<const C*>(p.rbuf) + ((size_t)slot * 5 + iu1) * vec;
+  C* RO = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + io) * vec;
+  H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + s_hc) * d.nb;
+  const long long nxy = (long long)d.nx * d.ny;
+  const int za = (int)((long long)blockIdx.x * d.nz / gridDim.x);
+  const int zb = (int)((long long)(blockIdx.x + 1) * d.nz / gridDim.x);
+  const int tid = threadIdx.x;
+  const int dx = kCombThreads % d.nxp, dy = kCombThreads / d.nxp;
+  typename AccOf<MODE>::type acc;
+  for (int z = za; z < zb; ++z) {
+    const long long zo = (long long)z * pe;
+    const int pl = recorded_plane(d, z);
+    int x = tid % d.nxp, y = tid / d.nxp;
+    for (long long e = tid; e < pe; e += 2 * kCombThreads) {
+      // two elements: e and e + 256 (the second may lie past the plane)
+      const long long e2 = e + kCombThreads;
+      int x2 = x + dx, y2 = y + dy;
+      if (x2 >= d.nxp) { x2 -= d.nxp; ++y2; }
+      const bool has2 = e2 < pe;
+      const C r1a = R1[zo + e], r2a = R2[zo + e], ua = U1[zo + e];
+      C r1b = O::zero(), r2b = O::zero(), ub = O::zero();
+      if (has2) { r1b = R1[zo + e2]; r2b = R2[zo + e2]; ub = U1[zo + e2]; }
+      const C ra = ST::combine(a1, r1a, a2, r2a, aA, ua);   // Eq. rvec
+      RO[zo + e] = ra;
+      if (x < d.nx) {
+        acc.add_r(ra);
+        if (pl >= 0) hist[(size_t)pl * nxy + (size_t)y * d.nx + x] = O::hi(ra);
+      }
+      if (has2) {
+        const C rb = ST::combine(a1, r1b, a2, r2b, aA, ub);
+        RO[zo + e2] = rb;
+        if (x2 < d.nx) {
+          acc.add_r(rb);
+          if (pl >= 0) hist[(size_t)pl * nxy + (size_t)y2 * d.nx + x2] = O::hi(rb);
+        }
+      }
+      x = x2 + dx;
+      y = y2 + dy;
+      if (x >= d.nxp) { x -= d.nxp; ++y; }
+    }
+  }
+  double v5[5];
+  acc.get(v5);
+  block_sum_lane0<5>(v5, s_red);
+  if (tid == 0) {
+    double* dst = p.partials + ((size_t)slot * d.npart + d.ctas_per_slot + blockIdx.x) * 8;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dst[k] = v5[k];
+  }
+}
+
+// Stencil: CTA = a 32 x TY tile of one slot and a z-range, one thread per tile point (one warp per
+// tile row).  Per z-plane one TMA transfer brings the (32 + 4) x (TY + 2R) box of r_n into a ring of
+// depth + R + 1 shared-memory stages; each thread keeps its own column's r_n on the last 2R + 1
+// planes in registers (ring rotated by unrolling, no moves) and takes its x and y neighbours from
+// the stage of the plane it evaluates.  One barrier per plane.
+constexpr int kMaxStagesS = kMaxDepth + 3;
+
+// The potential of the plane being evaluated arrives by TMA with the plane of r_n.  There is no
+// CTA-wide barrier per plane: every stage has a "full" mbarrier (the TMA transaction count) and an
+// "empty" one on which each warp arrives once it is done with the stage; thread 0 waits for a stage
+// to be empty before it refills it, so warps run up to the prefetch depth apart.
+template <int MODE, int R, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR,
+                                                             const __grid_constant__ CUtensorMap tmV) {
+  typedef Ops<MODE> O;
+  typedef typename O::C C;
+  typedef typename O::VT VT;
+  constexpr int Q = 2 * R + 1;
+  constexpr int BW = kTileX + 2 * kUBoxOff;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ ScalarShared S;
+  __shared__ int s_last;
+  __shared__ volatile int s_abort;
+  __shared__ __align__(8) unsigned long long bars[kMaxStagesS];     // full: TMA bytes landed
+  __shared__ __align__(8) unsigned long long ebars[kMaxStagesS];    // empty: every warp done with it
+
+  const int slot = blockIdx.y;
+  SlotState* st = p.slots + slot;
+  if (st->status != SLOT_RUNNING) return;
+  const SolveDims& d = p.d;
+  const int kDepth = p.depth;
+  const int NS = kDepth + R + 1;   // the stage of plane c is read R steps after its arrival
+  const int TY = d.tile_y;
+  const int EY = TY + 2 * R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cta = blockIdx.x;
+  const int tz = cta % d.nzchunks;
+  const int txy = cta / d.nzchunks;
+  const int tx = txy % d.tiles_x, ty = txy / d.tiles_x;
+  const int z0 = tz * d.zchunk;
+  const int z1 = min(z0 + d.zchunk, d.nz);
+  const int x0 = tx * kTileX, y0 = ty * TY;
+  const int gx = x0 + lane, gy = y0 + warp;
+  const bool own = gx < d.nx && gy < d.ny;
+  const long long plane_elems = (long long)d.nxp * d.ny;
+
+  // shared memory: per stage the box of r_n (plane q) and the tile of V (plane q - R)
+  const size_t PBb = (size_t)BW * EY * sizeof(C);
+  const int PE = (int)(((PBb + 127) & ~(size_t)127) / sizeof(C));
+  const size_t PVb = (size_t)kTileX * TY * sizeof(VT);
+  const int PV = (int)(((PVb + 127) & ~(size_t)127) / sizeof(VT));
+  C* ring = (C*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  VT* vring = (VT*)(ring + (size_t)NS * PE);
+
+  struct Coefs {
+    typename O::Real zre, zim, mh1, mh2;
+    int n;
+  };
+  __shared__ Coefs sc;
+  if (tid == 0) {
+    const double2 Zs0 = st->Zs;
+    sc.zre = O::real(Zs0.x - p.hd);
+    sc.zim = O::real(Zs0.y);
+    sc.mh1 = O::real(-p.hk1);
+    sc.mh2 = O::real(-p.hk2);
+    sc.n = st->n;
+  }
+  __syncthreads();
+  const int n = sc.n;
+  const int io = n % 3, iuo = 3 + n % 2;
+  const long long vec = (long long)d.nz * plane_elems;
+  C* uout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + iuo) * vec;
+  const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
+
+  constexpr int mR = (MODE == RSFD_DF64) ? 4 : 2;
+  constexpr int mV = (MODE == RSFD_DF64) ? 2 : 1;
+  const int xr = mR * (x0 - kUBoxOff), yb = y0 - R, xv = mV * x0;
+  const int nsteps = (z1 - z0) + 2 * R;
+  const int wr = slot * 5 + io;
+  auto issue = [&](int bnd) {
+    const int k = bnd % NS;
+    const uint32_t bar = smem_u32(&bars[k]);
+    mbar_expect_tx(bar, (uint32_t)(PBb + PVb));
+    tma_load_4d(smem_u32(ring + (size_t)k * PE), &tmR, xr, yb, z0 - R + bnd, wr, bar);
+    tma_load_3d(smem_u32(vring + (size_t)k * PV), &tmV, xv, y0, z0 - 2 * R + bnd, bar);
+  };
+  const int nwarps = blockDim.x >> 5;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(smem_u32(&bars[k]), 1);
+      mbar_init(smem_u32(&ebars[k]), (uint32_t)nwarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  if (tid == 0) {
+    for (int bnd = 0; bnd < kDepth && bnd < nsteps; ++bnd) issue(bnd);
+    issued = min(kDepth, nsteps);
+  }
+  typename AccOf<MODE>::type acc;
+  // step s: plane q = z0 - R + s and the potential of plane c = q - R arrive in stage s % NS; from
+  // step 2R on, A r_n on plane c, whose r_n box is in stage (s - R) % NS.  A stage is released after
+  // its plane served as plane c (R steps after it arrived).
+  int ist = 0, par = 0, ic = NS - R, s = 0;
+  const int oc = (warp + R) * BW + lane + kUBoxOff;   // this thread's point in a stage
+  const int ov = warp * kTileX + lane;                // and in the potential's tile
+  auto fail_now = [&]() {
+    s_abort = 1;
+    atomicExch(p.error_flag, 1);
+  };
+  auto begin_step = [&]() -> bool {
+    if (tid == 0 && s + kDepth < nsteps && !s_abort) {
+      const int b = s + kDepth;
+      // the stage's previous bundle (b - NS) must have been released by every warp
+      if (b >= NS && !mbar_wait(smem_u32(&ebars[b % NS]), (uint32_t)(((b / NS) - 1) & 1), first_wait_cap(d))) {
+        fail_now();
+      } else {
+        issue(b);
+        issued = b + 1;
+      }
+    }
+    if (s_abort) return false;
+    if (!mbar_wait(smem_u32(&bars[ist]), (uint32_t)par, first_wait_cap(d))) {
+      fail_now();
+      return false;
+    }
+    return true;
+  };
+  auto end_step = [&]() -> bool {
+    __syncwarp();
+    if (s >= R && lane == 0) mbar_arrive(smem_u32(&ebars[ic]));   // stage of bundle s - R
+    if (s_abort) return false;
+    if (++ist == NS) { ist = 0; par ^= 1; }
+    if (++ic == NS) ic = 0;
+    ++s;
+    return true;
+  };
+  bool ok = true;
+  C zq[Q];
+#pragma unroll
+  for (int t = 0; t < Q; ++t) zq[t] = O::zero();
+#pragma unroll
+  for (int t = 0; t < 2 * R; ++t) {
+    if (ok && s < nsteps) {
+      ok = begin_step();
+      if (!ok) break;
+      const C own_v = ring[(size_t)ist * PE + oc];
+      if (t == 0) zq[0] = own_v;
+      if (t == 1) zq[1 % Q] = own_v;
+      if (t == 2) zq[2 % Q] = own_v;
+      if (t == 3) zq[3 % Q] = own_v;
+      ok = end_step();
+    }
+  }
+  auto steady = [&](auto j_c) {
+    constexpr int PH = (2 * R + decltype(j_c)::value) % Q;   // ring slot of plane q
+    constexpr int CC = (PH + Q - R) % Q;                     // ring slot of plane c = q - R
+    if (!begin_step()) {
+      ok = false;
+      return;
+    }
+    zq[PH] = ring[(size_t)ist * PE + oc];
+    const int c = z0 - 2 * R + s;
+    const C* P0 = ring + (size_t)ic * PE;
+    C n1[6], n2[6];
+    n1[0] = zq[(CC + Q - 1) % Q];
+    n1[1] = zq[(CC + 1) % Q];
+    n1[2] = P0[oc - 1];
+    n1[3] = P0[oc + 1];
+    n1[4] = P0[oc - BW];
+    n1[5] = P0[oc + BW];
+    if (R == 2) {
+      n2[0] = zq[(CC + Q - 2) % Q];
+      n2[1] = zq[(CC + 2) % Q];
+      n2[2] = P0[oc - 2];
+      n2[3] = P0[oc + 2];
+      n2[4] = P0[oc - 2 * BW];
+      n2[5] = P0[oc + 2 * BW];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) n2[m] = O::zero();
+    }
+    if (own) {
+      const C rc = zq[CC];
+      const VT v = vring[(size_t)ist * PV + ov];
+      const C u = Stencil<MODE, R>::applyA(rc, n1, n2, v, zre, zim, mh1, mh2);
+      acc.add_ra(rc, u);
+      uout[(long long)c * plane_elems + (long long)gy * d.nxp + gx] = u;
+    }
+    ok = end_step();
+  };
+  while (ok && s < nsteps) {
+    steady(std::integral_constant<int, 0>());
+    if (ok && s < nsteps) steady(std::integral_constant<int, 1>());
+    if (ok && s < nsteps) steady(std::integral_constant<int, 2>());
+    if (R == 2) {
+      if (ok && s < nsteps) steady(std::integral_constant<int, 3>());
+      if (ok && s < nsteps) steady(std::integral_constant<int, 4>());
+    }
+  }
+  (void)ok;
+  __syncthreads();   // every thread, finished or stopped by an expired wait
+  if (s_abort) {
+    // drain the transfers still in flight: per stage, the last bundle thread 0 issued into it (the
+    // earlier ones on that stage completed before it was refilled)
+    if (tid == 0) {
+      for (int bnd = max(0, issued - NS); bnd < issued; ++bnd)
+        mbar_wait(smem_u32(&bars[bnd % NS]), (uint32_t)((bnd / NS) & 1));
+    }
+    return;
+  }
+  double v5[5];
+  acc.get(v5);
+  if (pass_finish(p, slot, cta, v5, S, s_last)) {
+    if (p.has_proj) {
+      if (tid == 0) {
+        double* o = p.pdots + (size_t)slot * 8;
+        o[0] = S.rr.x;
+        o[1] = S.rr.y;
+        o[2] = S.rAr.x;
+        o[3] = S.rAr.y;
+        o[4] = S.nrm2;
+      }
+    } else {
+      scalar_step(p, slot, S);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // nonlocal projector term (separable Kleinman-Bylander form, Sec. II A):
 //   V_nl r = sum_a E_a c_a p_a,   c_a = h^3 p_a^T r,
 // so with u_loc = (Z_s - H_loc) r from the pass,
@@ -1838,9 +2205,10 @@ template <typename X, typename G>
 __global__ void writeout_kernel(SolveDims d, const void* xbuf, void* G0, const int* list) {
   const int slot = list[2 * blockIdx.y], col = list[2 * blockIdx.y + 1];
   const long long knb = (long long)d.K * d.nb;
+  const long long onb = (long long)d.kreq * d.nb;   // the set's energies come first in x_b
   const X* x = reinterpret_cast<const X*>(xbuf) + (size_t)slot * knb;
   G* g = reinterpret_cast<G*>(G0);
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < knb; t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < onb; t += (long long)gridDim.x * blockDim.x) {
     const long long k = t / d.nb, row = t - k * d.nb;
     g[((size_t)k * d.ncols + col) * d.nb + row] = convx(x[t], (G*)nullptr);
   }
@@ -1848,7 +2216,7 @@ __global__ void writeout_kernel(SolveDims d, const void* xbuf, void* G0, const i
 
 template <int MODE, int R>
 cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
-                          int hist_len, cudaStream_t st) {
+                          int hist_len, cudaStream_t st, cudaEvent_t mid, bool mid_external) {
   typedef typename Ops<MODE>::C C;
   typedef typename Ops<MODE>::VT VT;
   PassParams p;
@@ -1871,10 +2239,24 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.maxit = maxit;
   p.hist_len = hist_len;
   p.depth = d.depth;
-  p.stored_u = d.kind == RSFD_PASS_STORED;
+  p.stored_u = d.kind == RSFD_PASS_STORED || d.kind == RSFD_PASS_SPLIT;
   p.has_proj = b.n_atoms > 0;
   p.pdots = b.pdots;
   dim3 grid(d.ctas_per_slot, d.W);
+  if (d.kind == RSFD_PASS_SPLIT) {
+    combine_kernel<MODE><<<dim3(d.ctas_c, d.W), kCombThreads, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (mid) {   // profiling: the boundary between the combine and the stencil launch
+      e = mid_external ? cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal) : cudaEventRecord(mid, st);
+      if (e != cudaSuccess) return e;
+    }
+    const size_t smem = split_smem(MODE, R, d.tile_y, d.depth);
+    const int thr = split_threads(d.tile_y);
+    if (thr <= 256) stencil_kernel<MODE, R, 256, 3><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmV);
+    else stencil_kernel<MODE, R, 512, 1><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmV);
+    return cudaGetLastError();
+  }
   if (d.kind == RSFD_PASS_STORED) {
     const size_t smem = passu_smem(MODE, R, d.tile_y, d.depth, d.tile_x);
     const int thr = passu_threads(d.rows, R, d.tile_y, d.tile_x);
@@ -1906,6 +2288,22 @@ size_t pass_smem(int prec, int R, int tile_y, int depth) {
   return (size_t)(R + 1 + depth + stages + R + 2) * pc + stages * pv + 128;
 }
 int pass_max_depth() { return kMaxDepth; }
+int split_threads(int tile_y) { return 32 * tile_y; }
+size_t split_smem(int prec, int R, int tile_y, int depth) {
+  const size_t es = prec == RSFD_MIXED ? 8 : 16;
+  const size_t pb = ((size_t)(kTileX + 2 * kUBoxOff) * (tile_y + 2 * R) * es + 127) & ~(size_t)127;
+  // per TMA stage the box of r_n and the tile of the potential
+  const size_t vs = prec == RSFD_MIXED ? 4 : 8;
+  const size_t pv = ((size_t)kTileX * tile_y * vs + 127) & ~(size_t)127;
+  return (size_t)(depth + R + 1) * (pb + pv) + 128;
+}
+int split_combine_ctas(int nz, int W, int sms) {
+  // about eight 256-thread CTAs per SM over all slots, at least one plane each
+  int c = (8 * sms + W - 1) / W;
+  if (c > nz) c = nz;
+  if (c > 64) c = 64;
+  return c < 1 ? 1 : c;
+}
 int passu_box_x(int tile_x) { return passu_box_w(tile_x); }
 int passu_box_off() { return kUBoxOff; }
 // tile threads (one x column and P rows each) plus the frame warps
@@ -1943,6 +2341,16 @@ cudaError_t kernels_init() {
   RSFD_ATTR(RSFD_DF64, 1)
   RSFD_ATTR(RSFD_DF64, 2)
 #undef RSFD_ATTR
+#define RSFD_ATTR_S(M, R)                                                                                \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<M, R, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<M, R, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  RSFD_ATTR_S(RSFD_FP64, 1)
+  RSFD_ATTR_S(RSFD_FP64, 2)
+  RSFD_ATTR_S(RSFD_MIXED, 1)
+  RSFD_ATTR_S(RSFD_MIXED, 2)
+  RSFD_ATTR_S(RSFD_DF64, 1)
+  RSFD_ATTR_S(RSFD_DF64, 2)
+#undef RSFD_ATTR_S
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -1963,15 +2371,15 @@ cudaError_t kernels_init() {
 }
 
 cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
-                        int maxit, int hist_len, cudaStream_t st) {
+                        int maxit, int hist_len, cudaStream_t st, cudaEvent_t mid, bool mid_external) {
   if (prec == RSFD_FP64)
-    return d.R == 1 ? launch_pass_t<RSFD_FP64, 1>(d, b, c, tol, maxit, hist_len, st)
-                    : launch_pass_t<RSFD_FP64, 2>(d, b, c, tol, maxit, hist_len, st);
+    return d.R == 1 ? launch_pass_t<RSFD_FP64, 1>(d, b, c, tol, maxit, hist_len, st, mid, mid_external)
+                    : launch_pass_t<RSFD_FP64, 2>(d, b, c, tol, maxit, hist_len, st, mid, mid_external);
   if (prec == RSFD_MIXED)
-    return d.R == 1 ? launch_pass_t<RSFD_MIXED, 1>(d, b, c, tol, maxit, hist_len, st)
-                    : launch_pass_t<RSFD_MIXED, 2>(d, b, c, tol, maxit, hist_len, st);
-  return d.R == 1 ? launch_pass_t<RSFD_DF64, 1>(d, b, c, tol, maxit, hist_len, st)
-                  : launch_pass_t<RSFD_DF64, 2>(d, b, c, tol, maxit, hist_len, st);
+    return d.R == 1 ? launch_pass_t<RSFD_MIXED, 1>(d, b, c, tol, maxit, hist_len, st, mid, mid_external)
+                    : launch_pass_t<RSFD_MIXED, 2>(d, b, c, tol, maxit, hist_len, st, mid, mid_external);
+  return d.R == 1 ? launch_pass_t<RSFD_DF64, 1>(d, b, c, tol, maxit, hist_len, st, mid, mid_external)
+                  : launch_pass_t<RSFD_DF64, 2>(d, b, c, tol, maxit, hist_len, st, mid, mid_external);
 }
 
 template <int MODE, int R>

@@ -96,6 +96,31 @@ __global__ void copy_c128(const double2* src, double2* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = src[i];
 }
+__device__ __forceinline__ void cvt(double2 a, double2& b) { b = a; }
+__device__ __forceinline__ void cvt(double2 a, float2& b) { b = make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ void cvt(float2 a, double2& b) { b = make_double2((double)a.x, (double)a.y); }
+// dst[b ds + i] = src[b ss + i] for i < n, b < batch (a block of leading columns of each energy's
+// matrix, with a type conversion where the types differ)
+template <typename S, typename D>
+__global__ void copy_batched(const S* src, long long ss, D* dst, long long ds, long long n, int batch) {
+  const long long tot = n * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n, i = t - b * n;
+    cvt(src[b * ss + i], dst[b * ds + i]);
+  }
+}
+// dst[b ds + off + i] = 0 for i < n, b < batch
+template <typename D>
+__global__ void zero_batched(D* dst, long long ds, long long off, long long n, int batch) {
+  const long long tot = n * batch;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n, i = t - b * n;
+    D z;
+    z.x = 0;
+    z.y = 0;
+    dst[b * ds + off + i] = z;
+  }
+}
 
 // M = I - G0 * blockdiag(SL, SR) is formed by two GEMMs after M = I.
 __global__ void set_identity(double2* M, int nb, int batch) {
@@ -370,8 +395,12 @@ rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* 
   const long long n2 = (long long)nb * nb, s2 = (long long)ns * ns;
   const bool fp64in = handle_prec(h) != RSFD_MIXED;
   const int nref = handle_dyson_refine(h);
-  // per energy: M, X, R (c128), G0 copy when the input is complex64, F and the FP32 solve (c64)
-  const long long per = n2 * (3 * 16 + (fp64in ? 0 : 16) + 2 * 8) + (long long)nb * 8 + 64;
+  // columns solved: all nb, or the left slab's ns (the block of G_bb the transmission uses)
+  const int nc = handle_dyson_cols(h) == 1 ? ns : nb;
+  const long long sx = (long long)nb * nc;
+  // per energy: M (c128), X, R and the compact right-hand side (c128, nb x nc), the G0 copy when the
+  // input is complex64, F (c64) and the FP32 solve (c64, nb x nc)
+  const long long per = n2 * (16 + (fp64in ? 0 : 16) + 8) + sx * (3 * 16 + 8) + (long long)nb * 8 + 64;
   size_t free_b = 0, tot_b = 0;
   DY_CK(h, cudaMemGetInfo(&free_b, &tot_b));
   long long kc = (long long)(0.6 * (double)free_b) / per;
@@ -379,14 +408,15 @@ rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* 
   if (kc < 1) kc = 1;
   const int Kc = (int)kc;
   rsfd_status s;
-  void *pM, *pX, *pR, *pF, *pPiv, *pRed, *pG0;
+  void *pM, *pX, *pR, *pF, *pPiv, *pRed, *pG0, *pB;
   if ((s = handle_ensure(h, 1, n2 * Kc * sizeof(double2), &pM)) != RSFD_OK) return s;
-  if ((s = handle_ensure(h, 3, n2 * Kc * sizeof(double2), &pX)) != RSFD_OK) return s;
-  if ((s = handle_ensure(h, 4, n2 * Kc * sizeof(double2), &pR)) != RSFD_OK) return s;
-  if ((s = handle_ensure(h, 2, 2 * n2 * Kc * sizeof(float2), &pF)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 3, sx * Kc * sizeof(double2), &pX)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, sx * Kc * sizeof(double2), &pR)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 2, (n2 + sx) * Kc * sizeof(float2), &pF)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 5, ((long long)Kc * (2 * nb + 1) + 1) * sizeof(int), &pPiv)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pRed)) != RSFD_OK) return s;
   if (!fp64in && (s = handle_ensure(h, 0, n2 * Kc * sizeof(double2), &pG0)) != RSFD_OK) return s;
+  if (nc < nb && (s = handle_ensure(h, 7, sx * Kc * sizeof(double2), &pB)) != RSFD_OK) return s;
   if ((s = handle_begin(h)) != RSFD_OK) return s;
   cudaStream_t st = handle_stream(h);
   double2* dM = (double2*)pM;
@@ -404,13 +434,19 @@ rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* 
   std::vector<int> hinfo(K, 0);
   for (int k0 = 0; k0 < K; k0 += Kc) {
     const int kb = K - k0 < Kc ? K - k0 : Kc;
-    const long long tot = n2 * kb;
+    const long long tot = n2 * kb, totx = sx * kb;
     const double2* g0;
     if (fp64in) {
       g0 = (const double2*)G0 + n2 * k0;
     } else {
       to_c128<float2><<<grid_for(tot), 256, 0, st>>>((const float2*)G0 + n2 * k0, (double2*)pG0, tot);
       g0 = (const double2*)pG0;
+    }
+    // right-hand sides: G0's first nc columns of every energy, compact (stride sx)
+    const double2* b0 = g0;
+    if (nc < nb) {
+      copy_batched<double2, double2><<<grid_for(totx), 256, 0, st>>>(g0, n2, (double2*)pB, sx, sx, kb);
+      b0 = (const double2*)pB;
     }
     const double2* sl = (const double2*)SL + s2 * k0;
     const double2* sr = (const double2*)SR + s2 * k0;
@@ -420,22 +456,27 @@ rsfd_status dyson_tc_run(Handle* h, const void* G0, const void* SL, const void* 
     to_f32_c<<<grid_for(tot), 256, 0, st>>>(dM, dF, tot);
     DY_CK(h, cudaMemsetAsync(info, 0, kb * sizeof(int), st));
     DY_CK(h, getrf_f32_tc(st, dF, nb, kb, piv, info, err));
-    DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, g0, nb, dXf, perm, err));
-    set_f32_to_c128<<<grid_for(tot), 256, 0, st>>>(dX, dXf, tot);
+    DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, b0, nc, dXf, perm, err));
+    set_f32_to_c128<<<grid_for(totx), 256, 0, st>>>(dX, dXf, totx);
     for (int it = 0; it < nref; ++it) {
-      copy_c128<<<grid_for(tot), 256, 0, st>>>(g0, dR, tot);
-      zgemm(st, kb, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
-      DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, (const double2*)dR, nb, dXf, perm, err));
-      add_f32_to_c128<<<grid_for(tot), 256, 0, st>>>(dX, dXf, tot);
+      copy_c128<<<grid_for(totx), 256, 0, st>>>(b0, dR, totx);
+      zgemm(st, kb, nb, nc, nb, m1, dM, nb, n2, 0, dX, nb, sx, one, dR, nb, sx);
+      DY_CK(h, getrs_f32_tc(st, dF, piv, nb, kb, (const double2*)dR, nc, dXf, perm, err));
+      add_f32_to_c128<<<grid_for(totx), 256, 0, st>>>(dX, dXf, totx);
     }
     if (refres) {
-      copy_c128<<<grid_for(tot), 256, 0, st>>>(g0, dR, tot);
-      zgemm(st, kb, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
-      frob2_batched<<<kb, 256, 0, st>>>(dR, n2, red + k0);
-      frob2_batched<<<kb, 256, 0, st>>>(g0, n2, red + K + k0);
+      copy_c128<<<grid_for(totx), 256, 0, st>>>(b0, dR, totx);
+      zgemm(st, kb, nb, nc, nb, m1, dM, nb, n2, 0, dX, nb, sx, one, dR, nb, sx);
+      frob2_batched<<<kb, 256, 0, st>>>(dR, sx, red + k0);
+      frob2_batched<<<kb, 256, 0, st>>>(b0, sx, red + K + k0);
     }
-    if (fp64in) copy_c128<<<grid_for(tot), 256, 0, st>>>(dX, (double2*)G + n2 * k0, tot);
-    else from_c128_f<<<grid_for(tot), 256, 0, st>>>(dX, (float2*)G + n2 * k0, tot);
+    if (fp64in) {
+      copy_batched<double2, double2><<<grid_for(totx), 256, 0, st>>>(dX, sx, (double2*)G + n2 * k0, n2, sx, kb);
+      if (nc < nb) zero_batched<double2><<<grid_for(tot - totx), 256, 0, st>>>((double2*)G + n2 * k0, n2, sx, n2 - sx, kb);
+    } else {
+      copy_batched<double2, float2><<<grid_for(totx), 256, 0, st>>>(dX, sx, (float2*)G + n2 * k0, n2, sx, kb);
+      if (nc < nb) zero_batched<float2><<<grid_for(tot - totx), 256, 0, st>>>((float2*)G + n2 * k0, n2, sx, n2 - sx, kb);
+    }
     DY_CK(h, cudaGetLastError());
     DY_CK(h, cudaMemcpyAsync(hinfo.data() + k0, info, kb * sizeof(int), cudaMemcpyDeviceToHost, st));
   }
@@ -465,8 +506,11 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
   if ((s = handle_ensure(h, 0, n2 * K * sizeof(double2), &pG0)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 1, n2 * K * sizeof(double2), &pM)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 2, n2 * K * sizeof(double2), &pLU)) != RSFD_OK) return s;
-  if ((s = handle_ensure(h, 3, n2 * K * sizeof(double2), &pX)) != RSFD_OK) return s;
-  if ((s = handle_ensure(h, 4, n2 * K * sizeof(double2), &pR)) != RSFD_OK) return s;
+  // columns solved: all nb, or the left slab's ns (the block of G_bb the transmission uses)
+  const int nc = handle_dyson_cols(h) == 1 ? ns : nb;
+  const long long sx = (long long)nb * nc, totx = sx * K;
+  if ((s = handle_ensure(h, 3, sx * K * sizeof(double2), &pX)) != RSFD_OK) return s;
+  if ((s = handle_ensure(h, 4, sx * K * sizeof(double2), &pR)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 5, (long long)K * (nb + 1) * sizeof(int), &pPiv)) != RSFD_OK) return s;
   if ((s = handle_ensure(h, 6, (long long)2 * K * sizeof(double), &pRed)) != RSFD_OK) return s;
   if ((s = handle_begin(h)) != RSFD_OK) return s;
@@ -491,27 +535,40 @@ rsfd_status dyson_run(Handle* h, const void* G0, const void* SL, const void* SR,
   copy_c128<<<grid_for(tot), 256, 0, st>>>(dM, dLU, tot);
   DY_CK(h, cudaMemsetAsync(info, 0, K * sizeof(int), st));
   getrf_blocked(st, dLU, nb, K, piv, info);
-  copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dX, tot);
+  // right-hand sides: the first nc columns of every energy, compact (stride sx)
+  const double2* b0 = dG0;
+  if (nc < nb) {
+    void* pB = nullptr;
+    if ((s = handle_ensure(h, 7, sx * K * sizeof(double2), &pB)) != RSFD_OK) return s;
+    copy_batched<double2, double2><<<grid_for(totx), 256, 0, st>>>(dG0, n2, (double2*)pB, sx, sx, K);
+    b0 = (const double2*)pB;
+  }
+  copy_c128<<<grid_for(totx), 256, 0, st>>>(b0, dX, totx);
   {
-    dim3 g((nb + 127) / 128, K);
-    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dX, nb, nb);
+    dim3 g((nc + 127) / 128, K);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dX, nb, nc);
   }
   // iterative refinement in FP64
   for (int it = 0; it < 2; ++it) {
-    copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dR, tot);
-    zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
-    dim3 g((nb + 127) / 128, K);
-    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dR, nb, nb);
-    axpy_c128<<<grid_for(tot), 256, 0, st>>>(dX, dR, tot);
+    copy_c128<<<grid_for(totx), 256, 0, st>>>(b0, dR, totx);
+    zgemm(st, K, nb, nc, nb, m1, dM, nb, n2, 0, dX, nb, sx, one, dR, nb, sx);
+    dim3 g((nc + 127) / 128, K);
+    zgetrs_batched<<<g, 128, 0, st>>>(dLU, piv, dR, nb, nc);
+    axpy_c128<<<grid_for(totx), 256, 0, st>>>(dX, dR, totx);
   }
   if (refres) {
-    copy_c128<<<grid_for(tot), 256, 0, st>>>(dG0, dR, tot);
-    zgemm(st, K, nb, nb, nb, m1, dM, nb, n2, 0, dX, nb, n2, one, dR, nb, n2);
-    frob2_batched<<<K, 256, 0, st>>>(dR, n2, red);
-    frob2_batched<<<K, 256, 0, st>>>(dG0, n2, red + K);
+    copy_c128<<<grid_for(totx), 256, 0, st>>>(b0, dR, totx);
+    zgemm(st, K, nb, nc, nb, m1, dM, nb, n2, 0, dX, nb, sx, one, dR, nb, sx);
+    frob2_batched<<<K, 256, 0, st>>>(dR, sx, red);
+    frob2_batched<<<K, 256, 0, st>>>(b0, sx, red + K);
   }
-  if (fp64) copy_c128<<<grid_for(tot), 256, 0, st>>>(dX, (double2*)G, tot);
-  else from_c128_f<<<grid_for(tot), 256, 0, st>>>(dX, (float2*)G, tot);
+  if (fp64) {
+    copy_batched<double2, double2><<<grid_for(totx), 256, 0, st>>>(dX, sx, (double2*)G, n2, sx, K);
+    if (nc < nb) zero_batched<double2><<<grid_for(tot - totx), 256, 0, st>>>((double2*)G, n2, sx, n2 - sx, K);
+  } else {
+    copy_batched<double2, float2><<<grid_for(totx), 256, 0, st>>>(dX, sx, (float2*)G, n2, sx, K);
+    if (nc < nb) zero_batched<float2><<<grid_for(tot - totx), 256, 0, st>>>((float2*)G, n2, sx, n2 - sx, K);
+  }
   DY_CK(h, cudaGetLastError());
   std::vector<int> hinfo(K);
   DY_CK(h, cudaMemcpyAsync(hinfo.data(), info, K * sizeof(int), cudaMemcpyDeviceToHost, st));

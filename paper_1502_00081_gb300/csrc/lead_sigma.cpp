@@ -18,8 +18,10 @@
 
 #include <math.h>
 
+#include <algorithm>
 #include <complex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rsfd_internal.cuh"
@@ -108,10 +110,13 @@ rsfd_status lead_sigma_uniform(int nx, int ny, double h, int fd_order, const dou
   std::vector<double> wx, wy, Ux, Uy;
   jacobi_eigh(kinetic_1d(nx, h, fd_order), nx, wx, Ux);
   jacobi_eigh(kinetic_1d(ny, h, fd_order), ny, wy, Uy);
+  // energies are independent: host threads take interleaved energies, each with its own scratch
+  const int nthr = std::max(1, std::min<int>(K, (int)std::min(64u, std::max(1u, std::thread::hardware_concurrency()))));
+  auto work = [&](int t0) {
   std::vector<zc> sig((size_t)nxy * R * R);      // per mode (j*nx + i), R x R block (a, c)
   std::vector<zc> T1((size_t)ny * nx * nx);       // [j][x][x']
   std::vector<zc> blk((size_t)nxy * nxy);
-  for (int k = 0; k < K; ++k) {
+  for (int k = t0; k < K; k += nthr) {
     const zc Z(E[k], eta);
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
@@ -176,6 +181,14 @@ rsfd_status lead_sigma_uniform(int nx, int ny, double h, int fd_order, const dou
             pl[1] = v.imag();
           }
       }
+  }
+  };
+  if (nthr == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthr; ++t) pool.emplace_back(work, t);
+    for (auto& th : pool) th.join();
   }
   (void)err;
   return RSFD_OK;

@@ -117,6 +117,7 @@ int handle_dyson_kind(Handle* h) {
   if (h->opts.dyson_kind != RSFD_DYSON_AUTO) return h->opts.dyson_kind;
   return h->prec == RSFD_FP64 ? RSFD_DYSON_FP64 : RSFD_DYSON_TC;
 }
+int handle_dyson_cols(Handle* h) { return h->opts.dyson_cols; }
 int handle_dyson_refine(Handle* h) {
   if (h->opts.dyson_refine > 0) return h->opts.dyson_refine;
   return h->prec == RSFD_FP64 ? 2 : 1;
@@ -206,7 +207,7 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
   const CUtensorMapDataType dt = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint64_t es = f64 ? 8 : 4;
   const cuuint64_t mR = h->prec == RSFD_DF64 ? 4 : 2, mV = h->prec == RSFD_DF64 ? 2 : 1;
-  const bool stored = kind == RSFD_PASS_STORED;
+  const bool stored = kind == RSFD_PASS_STORED || kind == RSFD_PASS_SPLIT;
   const cuuint64_t nvec = stored ? 5 : 3;
   const cuuint32_t EY = (cuuint32_t)(tile_y + (stored ? 2 : 4) * h->R);
   const cuuint32_t BX = (cuuint32_t)(stored ? passu_box_x(tile_x) : pass_box_x());
@@ -234,11 +235,12 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
 }
 
 static int resolve_kind(int, int opt) {
-  if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED) return opt;
+  if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED || opt == RSFD_PASS_SPLIT) return opt;
   return RSFD_PASS_STORED;
 }
 
 static size_t kind_smem(int prec, int R, int tile_y, int depth, int kind, int tile_x = 32) {
+  if (kind == RSFD_PASS_SPLIT) return split_smem(prec, R, tile_y, depth);
   return kind == RSFD_PASS_STORED ? passu_smem(prec, R, tile_y, depth, tile_x) : pass_smem(prec, R, tile_y, depth);
 }
 
@@ -249,6 +251,11 @@ static int resolve_rows(int opt) {
 
 static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget = 0, int tile_x = 32) {
   if (tile_y < 1) return false;
+  if (kind == RSFD_PASS_SPLIT) {
+    // one row per thread, 32-wide tiles, at most 16 rows (512 threads)
+    if (tile_x != 32 || rows != 1 || tile_y > 16) return false;
+    return split_smem(prec, R, tile_y, 1) <= (size_t)(216 * 1024);
+  }
   if (tile_x != 32) {
     // the 16-wide tile: one-row double-float stored pass with the default register budget only
     if (tile_x != 16 || kind != RSFD_PASS_STORED || prec != RSFD_DF64 || rows != 1 || budget != 0) return false;
@@ -270,6 +277,7 @@ static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget 
 // the taller tile).  Stored-product pass: 8 rows (measured fastest on the 64 x 64 x 128 workload for
 // both precisions: more CTAs per SM outweigh the larger frame), fewer on smaller grids.
 static int default_tile_y(int prec, int R, int ny, int kind, int rows) {
+  if (kind == RSFD_PASS_SPLIT) return std::max(1, std::min(8, ny));
   if (kind == RSFD_PASS_STORED) {
     const int ty = std::max(rows, std::min(8, (ny + rows - 1) / rows * rows));
     if (tile_ok(prec, R, ty, kind, rows)) return ty;
@@ -541,7 +549,7 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
   }
   if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0 || o->prefetch < 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
-  if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_STORED)
+  if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_SPLIT)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: bad pass_kind");
   if (o->pass_kind == RSFD_PASS_RECOMPUTE && h->n_atoms > 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the recompute pass has no projector term; use the stored pass");
@@ -573,6 +581,7 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
   if (o->iters_per_sync > kMaxHist)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: iters_per_sync must be <= " + std::to_string(kMaxHist));
   if (o->wait_cap < -1) return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: wait_cap must be >= -1");
+  if (o->dyson_cols < 0 || o->dyson_cols > 1) return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: dyson_cols must be 0 or 1");
   if (!(o->breakdown_tol >= 0.0) || !isfinite(o->breakdown_tol))
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: breakdown_tol must be finite and >= 0");
   h->opts = *o;
@@ -585,26 +594,37 @@ static rsfd_status rsfd_get_stats_impl(rsfd_handle h, rsfd_stats* out) {
   return RSFD_OK;
 }
 
-static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
-                              double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
-                              void* G0_bb, rsfd_col_info* info, double* final_res) {
+static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies,
+                              int32_t Kout, const double* aux_energies, int32_t n_aux, double eta, double tol,
+                              int32_t maxit, int32_t seed_kind, int32_t seed_index, void* G0_bb, rsfd_col_info* info,
+                              double* final_res) {
   if (!h) return fail(nullptr, RSFD_ERR_ARG, "rsfd_shifted_cocg: NULL handle");
   if (!cols || ncols < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: need ncols >= 1 columns");
-  if (!energies || K < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: need K >= 1 energies");
+  if (!energies || Kout < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: need K >= 1 energies");
+  if (n_aux < 0 || (n_aux > 0 && !aux_energies)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: bad auxiliary energies");
+  for (int k = 0; k < n_aux; ++k)
+    if (!isfinite(aux_energies[k])) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: non-finite auxiliary energy");
+  // the shifts the scalar recurrences carry: the K energies of the set, then the auxiliary ones
+  // (seed candidates only: no output, not needed for termination)
+  const int K = Kout + n_aux;
   if (!(eta > 0) || !isfinite(eta)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: eta must be positive");
   if (!(tol > 0) || !(tol < 1)) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: tol must lie in (0, 1)");
   if (maxit < 1) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: maxit must be >= 1");
   if (!G0_bb) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: G0_bb is NULL");
-  for (int k = 0; k < K; ++k)
+  for (int k = 0; k < Kout; ++k)
     if (!isfinite(energies[k])) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: non-finite energy");
   for (int c = 0; c < ncols; ++c)
     if (cols[c] < 0 || cols[c] >= h->N) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: column index out of range");
   int seed0 = 0;
-  if (seed_kind == RSFD_SEED_MID) seed0 = K / 2;
+  if (seed_kind == RSFD_SEED_MID) seed0 = Kout / 2;
   else if (seed_kind == RSFD_SEED_FIRST) seed0 = 0;
   else if (seed_kind == RSFD_SEED_INDEX) {
-    if (seed_index < 0 || seed_index >= K) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: seed_index out of range");
+    if (seed_index < 0 || seed_index >= Kout) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: seed_index out of range");
     seed0 = seed_index;
+  } else if (seed_kind == RSFD_SEED_AUX) {
+    if (seed_index < 0 || seed_index >= n_aux)
+      return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: seed_index out of range of the auxiliary energies");
+    seed0 = Kout + seed_index;
   } else {
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: bad seed_kind");
   }
@@ -625,10 +645,13 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   d.ntrack = (int)h->track.size();
   for (int e = 0; e < d.ntrack; ++e) d.track[e] = h->track[e];
   d.K = K;
+  d.kreq = Kout;
   d.ncols = ncols;
   d.kind = resolve_kind(prec, h->opts.pass_kind);
-  if (h->n_atoms > 0) d.kind = RSFD_PASS_STORED;   // the projector term follows the stored-product pass
-  d.nvec = d.kind == RSFD_PASS_STORED ? 5 : 3;
+  // the projector term follows a pass that stores A r (stored-product or split)
+  if (h->n_atoms > 0 && d.kind == RSFD_PASS_RECOMPUTE) d.kind = RSFD_PASS_STORED;
+  d.nvec = d.kind == RSFD_PASS_RECOMPUTE ? 3 : 5;
+  if (d.kind == RSFD_PASS_SPLIT) d.rows = 1;
   d.rows = resolve_rows(h->opts.rows_per_thread);
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
   d.regs = (prec == RSFD_DF64 && d.rows == 1 && d.kind == RSFD_PASS_STORED) ? h->opts.reg_budget : 0;
@@ -643,7 +666,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     d.depth = h->opts.prefetch;
   } else {
     d.depth = 1;
-    const int dmax = d.kind == RSFD_PASS_STORED ? 3 : pass_max_depth();
+    const int dmax = d.kind == RSFD_PASS_STORED ? 3 : (d.kind == RSFD_PASS_SPLIT ? 4 : pass_max_depth());
     for (int dp = dmax; dp >= 1; --dp)
       if (kind_smem(prec, h->R, d.tile_y, dp, d.kind, d.tile_x) <= (size_t)(216 * 1024)) {
         d.depth = dp;
@@ -653,7 +676,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   if (kind_smem(prec, h->R, d.tile_y, d.depth, d.kind, d.tile_x) > (size_t)(216 * 1024))
     return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: prefetch depth does not fit in shared memory");
   {
-    const int tw = d.kind == RSFD_PASS_STORED ? d.tile_x : pass_tile_x(h->R);
+    const int tw = d.kind == RSFD_PASS_RECOMPUTE ? pass_tile_x(h->R) : d.tile_x;
     d.tiles_x = (h->nx + tw - 1) / tw;
   }
   d.tiles_y = (h->ny + d.tile_y - 1) / d.tile_y;
@@ -671,6 +694,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   }
   d.nzchunks = (h->nz + d.zchunk - 1) / d.zchunk;
   d.ctas_per_slot = d.tiles_x * d.tiles_y * d.nzchunks;
+  d.ctas_c = 0;
   const int C = h->opts.iters_per_sync > 0 ? h->opts.iters_per_sync : 32;
   if (C > kMaxHist) return fail(h, RSFD_ERR_ARG, "rsfd_shifted_cocg: iters_per_sync too large");
   const long long vec = (long long)h->nxp * h->ny * h->nz;
@@ -680,7 +704,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     RSFD_CK(h, cudaMemGetInfo(&freeb, &totb));
     const size_t per_slot = (size_t)d.nvec * vec * vsz + 2 * (size_t)K * h->nr * vsz + (size_t)C * h->nr * hsz +
                             (size_t)K * C * sizeof(ShiftCoef) + (size_t)K * sizeof(ShiftState) +
-                            (size_t)d.ctas_per_slot * 64 + 256;
+                            (size_t)(d.ctas_per_slot + 64) * 64 + 256;
     const size_t have = h->rbuf.bytes + h->xbuf.bytes + h->pbuf.bytes + h->rhist.bytes + h->coef.bytes;
     const size_t budget = (size_t)(0.6 * (double)(freeb + have));
     if (h->opts.slots <= 0) {
@@ -688,6 +712,12 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     }
   }
   d.W = W;
+  if (d.kind == RSFD_PASS_SPLIT) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    d.ctas_c = split_combine_ctas(h->nz, W, sms);
+  }
+  d.npart = d.ctas_per_slot + d.ctas_c;
   const bool use_graphs = h->opts.use_graphs >= 0;
 
   // ---- workspace
@@ -702,7 +732,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   if ((s = ensure(h, h->eflag, 16)) != RSFD_OK) return s;
   if ((s = ensure(h, h->slots, (size_t)W * sizeof(SlotState))) != RSFD_OK) return s;
   if ((s = ensure(h, h->shifts, (size_t)W * K * sizeof(ShiftState))) != RSFD_OK) return s;
-  if ((s = ensure(h, h->partials, (size_t)W * d.ctas_per_slot * 8 * sizeof(double))) != RSFD_OK) return s;
+  if ((s = ensure(h, h->partials, (size_t)W * d.npart * 8 * sizeof(double))) != RSFD_OK) return s;
   if ((s = ensure(h, h->tickets, (size_t)W * sizeof(unsigned int))) != RSFD_OK) return s;
   if ((s = ensure(h, h->Z, (size_t)K * sizeof(double2))) != RSFD_OK) return s;
   if ((s = ensure(h, h->init_list, (size_t)W * 2 * sizeof(int))) != RSFD_OK) return s;
@@ -763,7 +793,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   RSFD_CK(h, cudaEventRecord(t0, st));
 
   std::vector<double2> Zh(K);
-  for (int k = 0; k < K; ++k) Zh[k] = make_double2(energies[k], eta);
+  for (int k = 0; k < K; ++k) Zh[k] = make_double2(k < Kout ? energies[k] : aux_energies[k - Kout], eta);
   RSFD_CK(h, cudaMemcpyAsync(b.Z, Zh.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
   RSFD_CK(h, cudaMemsetAsync(b.tickets, 0, W * sizeof(unsigned int), st));
   if (b.n_atoms > 0) RSFD_CK(h, cudaMemsetAsync(b.ptickets, 0, W * sizeof(unsigned int), st));
@@ -781,30 +811,50 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   memset(&h->stats, 0, sizeof(h->stats));
   h->stats.slots = W;
   h->stats.iters_per_sync = C;
+  // Pinned host staging, double-buffered by chunk parity: the slot states copied after a chunk,
+  // the error flag, the lists of finished and new columns, and the finished columns' residuals.
+  struct Pinned {
+    void* p = nullptr;
+    ~Pinned() { if (p) cudaFreeHost(p); }
+  };
+  Pinned pin_states, pin_lists, pin_res;
+  RSFD_CK(h, cudaMallocHost(&pin_states.p, 2 * (W * sizeof(SlotState) + 64)));
+  RSFD_CK(h, cudaMallocHost(&pin_lists.p, 2 * (4 * W * sizeof(int) + W * sizeof(long long) + 64)));
+  if (final_res) RSFD_CK(h, cudaMallocHost(&pin_res.p, (size_t)ncols * K * sizeof(double) + 64));
+  auto states_of = [&](int par) -> SlotState* {
+    return (SlotState*)((char*)pin_states.p + par * (W * sizeof(SlotState) + 64));
+  };
+  auto err_of = [&](int par) -> int* { return (int*)(states_of(par) + W); };
+  auto lists_of = [&](int par) -> int* {
+    return (int*)((char*)pin_lists.p + par * (4 * W * sizeof(int) + W * sizeof(long long) + 64));
+  };
+  auto grid_of = [&](int par) -> long long* { return (long long*)(lists_of(par) + 4 * W); };
+  double* res_host = (double*)pin_res.p;
+
   std::vector<int> slot_col(W, -1);
-  std::vector<int> list(2 * W);
-  std::vector<long long> init_grid(W);
-  std::vector<ShiftState> hsh(K);
+  std::vector<long long> valid_from(W, 0);   // first chunk whose copied state reflects the slot's column
   int next = 0;
   rsfd_status worst = RSFD_OK;
 
-  // load new columns into the given free slots
-  auto assign = [&](const std::vector<int>& free_slots) -> rsfd_status {
+  // load new columns into the given free slots (enqueued; the lists come from pinned staging set par)
+  auto assign = [&](const std::vector<int>& free_slots, int par, long long first_valid) -> rsfd_status {
     int n_init = 0;
+    int* list = lists_of(par) + 2 * W;
+    long long* init_grid = grid_of(par);
     for (int w : free_slots) {
       if (next >= ncols) break;
       list[2 * n_init] = w;
       list[2 * n_init + 1] = next;
       init_grid[n_init] = cols[next];
       slot_col[w] = next;
+      valid_from[w] = first_valid;
       ++next;
       ++n_init;
     }
     if (n_init == 0) return RSFD_OK;
-    RSFD_CK(h, cudaMemcpyAsync(b.init_list, list.data(), 2 * n_init * sizeof(int), cudaMemcpyHostToDevice, st));
-    RSFD_CK(h, cudaMemcpyAsync(b.init_grid, init_grid.data(), n_init * sizeof(long long), cudaMemcpyHostToDevice, st));
+    RSFD_CK(h, cudaMemcpyAsync(b.init_list, list, 2 * n_init * sizeof(int), cudaMemcpyHostToDevice, st));
+    RSFD_CK(h, cudaMemcpyAsync(b.init_grid, init_grid, n_init * sizeof(long long), cudaMemcpyHostToDevice, st));
     RSFD_CK(h, launch_slot_init(prec, d, b, n_init, seed0, st));
-    RSFD_CK(h, cudaStreamSynchronize(st));   // the host arrays are reused
     h->stats.n_other += 1;
     return RSFD_OK;
   };
@@ -812,24 +862,40 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   {
     std::vector<int> all(W);
     for (int w = 0; w < W; ++w) all[w] = w;
-    if ((s = assign(all)) != RSFD_OK) return s;
+    if ((s = assign(all, 0, 0)) != RSFD_OK) return s;
+    RSFD_CK(h, cudaStreamSynchronize(st));   // the pinned lists of set 0 are reused below
   }
 
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<cudaEvent_t> pev;
+  // One chunk: C passes, then the collapsed shift update of the C recorded steps.  Two graphs (and two
+  // sets of profiling events) alternate, so that chunk k + 1 can be enqueued before the host reads
+  // the events and slot states of chunk k.
+  struct Graphs {
+    cudaGraph_t g[2] = {nullptr, nullptr};
+    cudaGraphExec_t x[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev[2];
+    ~Graphs() {
+      for (int i = 0; i < 2; ++i) {
+        if (x[i]) cudaGraphExecDestroy(x[i]);
+        if (g[i]) cudaGraphDestroy(g[i]);
+        for (auto e : ev[i]) cudaEventDestroy(e);
+      }
+    }
+  } gr;
+  const bool split_ev = h->opts.profile && d.kind == RSFD_PASS_SPLIT;
   if (h->opts.profile) {
-    pev.resize(C + 2);
-    for (auto& e : pev) RSFD_CK(h, cudaEventCreate(&e));
+    for (int i = 0; i < 2; ++i) {
+      gr.ev[i].resize(C + 2 + (split_ev ? C : 0));   // [C + 2 + t]: between the split pass's two launches
+      for (auto& e : gr.ev[i]) RSFD_CK(h, cudaEventCreate(&e));
+    }
   }
   auto rec = [&](cudaEvent_t e) -> cudaError_t {
     return use_graphs ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
   };
-  // one chunk: C fused passes, then the collapsed shift update of the C recorded steps
-  auto issue_chunk = [&]() -> rsfd_status {
+  auto issue_chunk = [&](int par) -> rsfd_status {
+    std::vector<cudaEvent_t>& pev = gr.ev[par];
     for (int t = 0; t < C; ++t) {
       if (h->opts.profile) RSFD_CK(h, rec(pev[t]));
-      RSFD_CK(h, launch_pass(prec, d, b, coef, tol, maxit, C, st));
+      RSFD_CK(h, launch_pass(prec, d, b, coef, tol, maxit, C, st, split_ev ? pev[C + 2 + t] : nullptr, use_graphs));
       if (b.n_atoms > 0) RSFD_CK(h, launch_proj(prec, d, b, coef, tol, maxit, C, st));
     }
     if (h->opts.profile) RSFD_CK(h, rec(pev[C]));
@@ -838,60 +904,84 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     return RSFD_OK;
   };
   if (use_graphs) {
-    RSFD_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    rsfd_status cs = issue_chunk();
-    cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (cs != RSFD_OK) return cs;
-    RSFD_CK(h, ce);
-    RSFD_CK(h, cudaGraphInstantiate(&gexec, graph, 0));
-  }
-
-  int64_t iter_sum = 0;
-  int herr = 0;
-  for (;;) {
-    if (use_graphs) {
-      RSFD_CK(h, cudaGraphLaunch(gexec, st));
-    } else {
-      if ((s = issue_chunk()) != RSFD_OK) return s;
+    for (int i = 0; i < 2; ++i) {
+      RSFD_CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      rsfd_status cs = issue_chunk(i);
+      cudaError_t ce = cudaStreamEndCapture(st, &gr.g[i]);
+      if (cs != RSFD_OK) return cs;
+      RSFD_CK(h, ce);
+      RSFD_CK(h, cudaGraphInstantiate(&gr.x[i], gr.g[i], 0));
     }
-    h->stats.n_pass += C;
+  }
+  // chunk k, followed by the copy of the slot states and the error flag into staging set k % 2
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  struct EvPair {
+    cudaEvent_t* e;
+    ~EvPair() { for (int i = 0; i < 2; ++i) if (e[i]) cudaEventDestroy(e[i]); }
+  } evp{copied};
+  for (int i = 0; i < 2; ++i) RSFD_CK(h, cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
+  auto launch_chunk_k = [&](long long k) -> rsfd_status {
+    const int par = (int)(k & 1);
+    if (use_graphs) {
+      RSFD_CK(h, cudaGraphLaunch(gr.x[par], st));
+    } else {
+      rsfd_status cs = issue_chunk(par);
+      if (cs != RSFD_OK) return cs;
+    }
+    h->stats.n_pass += (int64_t)C * (d.kind == RSFD_PASS_SPLIT ? 2 : 1);   // the split pass launches twice
     h->stats.n_shift += 1;
     h->stats.n_other += 2 + (b.n_atoms > 0 ? 2 * C : 0);   // collapse coefficients, history reset, projectors
-    RSFD_CK(h, cudaMemcpyAsync(hs.data(), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
-    RSFD_CK(h, cudaMemcpyAsync(&herr, b.error_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RSFD_CK(h, cudaStreamSynchronize(st));
-    if (herr) {
+    RSFD_CK(h, cudaMemcpyAsync(states_of(par), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
+    RSFD_CK(h, cudaMemcpyAsync(err_of(par), b.error_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RSFD_CK(h, cudaEventRecord(copied[par], st));
+    return RSFD_OK;
+  };
+
+  int64_t iter_sum = 0;
+  if ((s = launch_chunk_k(0)) != RSFD_OK) return s;
+  for (long long k = 0;; ++k) {
+    // enqueue chunk k + 1 before reading chunk k's states; a slot that finished in chunk k is idle in
+    // chunk k + 1 (its kernels return at once), so its x_b is still final when it is written out
+    if ((s = launch_chunk_k(k + 1)) != RSFD_OK) return s;
+    const int par = (int)(k & 1);
+    RSFD_CK(h, cudaEventSynchronize(copied[par]));
+    if (*err_of(par)) {
       worst = RSFD_ERR_TIMEOUT;
       break;
     }
     if (h->opts.profile) {
+      std::vector<cudaEvent_t>& pev = gr.ev[par];
       for (int t = 0; t < C; ++t) {
         float a = 0;
         RSFD_CK(h, cudaEventElapsedTime(&a, pev[t], pev[t + 1]));
         h->stats.ms_pass += a;
+        if (split_ev) {
+          RSFD_CK(h, cudaEventElapsedTime(&a, pev[t], pev[C + 2 + t]));
+          h->stats.ms_combine += a;
+        }
       }
       float c2 = 0;
       RSFD_CK(h, cudaEventElapsedTime(&c2, pev[C], pev[C + 1]));
       h->stats.ms_shift += c2;
     }
-    // finished columns: write x_b into G0_bb, record the outcome, free the slot
+    const SlotState* hs = states_of(par);
+    // finished columns: write x_b into G0_bb (enqueued after chunk k + 1), record the outcome, free the slot
     std::vector<int> freed;
+    int* list = lists_of(par);
     int n_out = 0;
     for (int w = 0; w < W; ++w) {
-      if (slot_col[w] < 0 || hs[w].status == SLOT_RUNNING) continue;
+      if (slot_col[w] < 0 || k < valid_from[w] || hs[w].status == SLOT_RUNNING) continue;
       list[2 * n_out] = w;
       list[2 * n_out + 1] = slot_col[w];
       ++n_out;
     }
     if (n_out > 0) {
-      RSFD_CK(h, cudaMemcpyAsync(b.init_list, list.data(), 2 * n_out * sizeof(int), cudaMemcpyHostToDevice, st));
+      RSFD_CK(h, cudaMemcpyAsync(b.init_list, list, 2 * n_out * sizeof(int), cudaMemcpyHostToDevice, st));
       RSFD_CK(h, launch_writeout(prec, d, b, G0_bb, n_out, st));
       h->stats.n_other += 1;
-      RSFD_CK(h, cudaStreamSynchronize(st));
     }
-    for (int w = 0; w < W; ++w) {
-      if (slot_col[w] < 0 || hs[w].status == SLOT_RUNNING) continue;
-      const int c = slot_col[w];
+    for (int q = 0; q < n_out; ++q) {
+      const int w = list[2 * q], c = list[2 * q + 1];
       rsfd_status cs = RSFD_OK;
       if (hs[w].status == SLOT_MAXIT) cs = RSFD_ERR_NOT_CONVERGED;
       if (hs[w].status == SLOT_BREAKDOWN) cs = RSFD_ERR_BREAKDOWN;
@@ -903,20 +993,23 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
         info[c].status = cs;
         info[c].final_seed = hs[w].seed;
       }
-      if (final_res) {
-        RSFD_CK(h, cudaMemcpy(hsh.data(), b.shifts + (size_t)w * K, K * sizeof(ShiftState), cudaMemcpyDeviceToHost));
-        for (int k = 0; k < K; ++k) final_res[(size_t)c * K + k] = hsh[k].res;
+      if (final_res) {   // the residuals of the set's energies, read back before the slot is reused
+        RSFD_CK(h, cudaMemcpy2DAsync(res_host + (size_t)c * Kout, sizeof(double),
+                                     (const char*)(b.shifts + (size_t)w * K) + offsetof(ShiftState, res),
+                                     sizeof(ShiftState), sizeof(double), Kout, cudaMemcpyDeviceToHost, st));
       }
       slot_col[w] = -1;
       freed.push_back(w);
     }
     if (!freed.empty() && next < ncols) {
-      if ((s = assign(freed)) != RSFD_OK) return s;
+      if ((s = assign(freed, par, k + 2)) != RSFD_OK) return s;
     }
     bool any = false;
     for (int w = 0; w < W; ++w) any |= slot_col[w] >= 0;
     if (!any && next >= ncols) break;
   }
+  RSFD_CK(h, cudaStreamSynchronize(st));
+  if (final_res && worst != RSFD_ERR_TIMEOUT) memcpy(final_res, res_host, (size_t)ncols * Kout * sizeof(double));
   RSFD_CK(h, cudaEventRecord(t1, st));
   RSFD_CK(h, cudaEventSynchronize(t1));
   float ms = 0;
@@ -927,9 +1020,6 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   h->stats.shift_updates = (int64_t)cnt[0];
   h->stats.shift_slot_chunks = (int64_t)cnt[2];
   h->stats.slot_iterations = iter_sum;
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  for (auto& e : pev) cudaEventDestroy(e);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if ((s = handle_end(h)) != RSFD_OK) return s;
@@ -1041,9 +1131,36 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
   std::vector<rsfd_col_info> info(ncols);
   std::vector<double> res((size_t)ncols * K);
   std::vector<rsfd_solve_opts> cand;
-  const int kinds[2] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE};
+  const int kinds[3] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE, RSFD_PASS_SPLIT};
   const int zcs[3] = {0, h->nz, (h->nz + 1) / 2};
   for (int kind : kinds) {
+    if (kind == RSFD_PASS_SPLIT) {
+      // the split pass: tile height and z-chunk
+      const int tys[3] = {8, 4, 16};
+      const int pfs[2] = {0, 3};
+      for (int ty : tys) {
+        if (ty > h->ny && ty != 4) continue;
+        if (!tile_ok(h->prec, h->R, ty, kind, 1)) continue;
+        for (int zc : zcs)
+        for (int pf : pfs) {
+          if (zc > 0 && zc < 8) continue;
+          rsfd_solve_opts o = keep;
+          o.pass_kind = kind;
+          o.rows_per_thread = 0;
+          o.tile_y = ty;
+          o.z_chunk = zc;
+          o.reg_budget = 0;
+          o.tile_x = 0;
+          o.slots = ncols;
+          o.iters_per_sync = C;
+          o.profile = 1;
+          o.use_graphs = 0;
+          o.prefetch = pf;
+          cand.push_back(o);
+        }
+      }
+      continue;
+    }
     if (kind == RSFD_PASS_RECOMPUTE && h->n_atoms > 0) continue;
     const int rows_c[2] = {1, 2};
     for (int rows : rows_c) {
@@ -1102,7 +1219,7 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
   }
   best_o.profile = keep.profile;
   best_o.use_graphs = keep.use_graphs;
-  best_o.prefetch = keep.prefetch;
+  if (best_o.pass_kind != RSFD_PASS_SPLIT) best_o.prefetch = keep.prefetch;   // the split pass tunes its depth
   h->opts = best_o;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1361,7 +1478,14 @@ rsfd_status rsfd_get_stats(rsfd_handle h, rsfd_stats* out) {
 rsfd_status rsfd_shifted_cocg(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
                               double eta, double tol, int32_t maxit, int32_t seed_kind, int32_t seed_index,
                               void* G0_bb, rsfd_col_info* info, double* final_res) {
-  RSFD_GUARD(h, rsfd_shifted_cocg_impl(h, cols, ncols, energies, K, eta, tol, maxit, seed_kind, seed_index, G0_bb, info, final_res));
+  RSFD_GUARD(h, rsfd_shifted_cocg_impl(h, cols, ncols, energies, K, nullptr, 0, eta, tol, maxit, seed_kind, seed_index, G0_bb, info, final_res));
+}
+
+rsfd_status rsfd_shifted_cocg_aux(rsfd_handle h, const int64_t* cols, int32_t ncols, const double* energies, int32_t K,
+                                  const double* aux_energies, int32_t n_aux, double eta, double tol, int32_t maxit,
+                                  int32_t seed_kind, int32_t seed_index, void* G0_bb, rsfd_col_info* info,
+                                  double* final_res) {
+  RSFD_GUARD(h, rsfd_shifted_cocg_impl(h, cols, ncols, energies, K, aux_energies, n_aux, eta, tol, maxit, seed_kind, seed_index, G0_bb, info, final_res));
 }
 
 rsfd_status rsfd_dyson_boundary(rsfd_handle h, const void* G0_bb, const void* Sigma_L, const void* Sigma_R,

@@ -109,15 +109,18 @@ struct SolveDims {
   int R;              // stencil reach (fd_order / 2)
   int nface;          // boundary planes per side
   int nb;             // recorded rows per column: the boundary rows, then the tracked planes
-  int K;              // energies
+  int K;              // shifts carried by the scalar recurrences: the energies, then auxiliary seed energies
+  int kreq;           // energies of the set (written out, required for convergence): the first kreq
   int W;              // slots
   int tile_y;         // stencil tile height (y); the tile width in x is fixed by the kernel
   int depth;          // TMA prefetch depth of the pass kernel
   int tiles_x, tiles_y, zchunk, nzchunks, ctas_per_slot;
+  int ctas_c;         // split pass: CTAs per slot of the combine kernel (0 for the other forms)
+  int npart;          // partial-sum entries per slot: ctas_per_slot + ctas_c
   int ncols;
   int ntrack;         // interior planes recorded after the boundary planes
   int track[16];      // their z indices (rows 2 nface Nx Ny + e Nx Ny ...)
-  int kind;           // RSFD_PASS_RECOMPUTE or RSFD_PASS_STORED
+  int kind;           // RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED or RSFD_PASS_SPLIT
   int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
   int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
   int regs;           // register budget of the one-row double-float pass (0, 1)
@@ -178,9 +181,10 @@ struct PassConfig {
   int tile_x, tile_y;
 };
 
-// Launch one fused pass (stencil + seed update + dots + scalar step) over all slots.
+// Launch one pass (stencil + seed update + dots + scalar step) over all slots; for the split pass
+// an optional event is recorded between its combine and stencil launches (profiling).
 cudaError_t launch_pass(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
-                        int maxit, int hist_len, cudaStream_t st);
+                        int maxit, int hist_len, cudaStream_t st, cudaEvent_t mid = nullptr, bool mid_external = false);
 // Nonlocal projector term after a pass (stored-product form only): projections c_a = h^3 p_a^T r_n,
 // the corrected (r_n, A r_n) and the FP64 scalar step, then u_n -= sum_a E_a c_a p_a.
 cudaError_t launch_proj(int prec, const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol,
@@ -203,6 +207,9 @@ int passu_max_threads(int rows, int budget);
 int passu_box_x(int tile_x);
 int passu_box_off();
 int pass_max_depth();
+int split_threads(int tile_y);
+size_t split_smem(int prec, int R, int tile_y, int depth);
+int split_combine_ctas(int nz, int W, int sms);
 int pass_box_x();
 int pass_box_off();
 int pass_max_threads(int prec);
@@ -226,6 +233,7 @@ int handle_fd_order(Handle* h);
 double handle_h(Handle* h);
 int handle_dyson_kind(Handle* h);     // resolved: RSFD_DYSON_FP64 or RSFD_DYSON_TC
 int handle_dyson_refine(Handle* h);   // FP64 refinement steps of the Dyson solve
+int handle_dyson_cols(Handle* h);     // 0: every column of G_bb; 1: the left slab's columns only
 
 // Tensor-core building blocks of the Dyson step (tc_gemm.cu).  err: device flag set when a bounded
 // wait of the GEMM kernel expires.

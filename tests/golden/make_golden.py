@@ -9,7 +9,14 @@ comes from the CUDA library.  Output, for the 64x64x128 "sampled_columns_mixed" 
 * ``sampled_columns_mixed_oracle_iterations.json``: the oracle's seed iterations per column at the
   workload's own tolerance (used to scale the bounded CPU-baseline sample in bench.py).
 
+For the 8x8x12 "tiny_wire_fp64" workload (``--workload tiny_wire_fp64``, seconds):
+
+* ``tiny_wire_fp64_golden.npz``: the oracle's dense G_bb = [(Z - H_T - Sigma_L - Sigma_R)^{-1}]_{bb}
+  (Eq. GF2, LU) for every energy, with the lead self-energies of the oracle's closed form, and the
+  Fisher-Lee T(E) (Eq. TF) computed from it.
+
 Run:  python tests/golden/make_golden.py --ncols 2   (about an hour of single-core CPU time)
+      python tests/golden/make_golden.py --workload tiny_wire_fp64
 """
 
 import argparse
@@ -41,6 +48,24 @@ def one_column(args):
     return j, r.x, r.iterations, r.switches, r.status, time.time() - t0
 
 
+def tiny_wire(name):
+    from oracle.dense import g_dense
+    from oracle.leads import sigma_bloch
+    from oracle.transmission import transmission
+    p = make_problem(name)
+    b = boundary_rows(p.grid, p.n_face)
+    G, T = [], []
+    for E in p.energies:
+        Z = E + 1j * p.eta
+        SL, SR = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
+        Gd = g_dense(p, Z, SL, SR, rows=b, cols=b)
+        G.append(Gd)
+        T.append(transmission(Gd, SL, SR)[0])
+    np.savez_compressed(os.path.join(HERE, f"{name}_golden.npz"), rows=b, energies=p.energies, eta=p.eta,
+                        G_bb=np.stack(G), T=np.array(T))
+    print("done", name, np.array(T))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="sampled_columns_mixed")
@@ -48,6 +73,9 @@ def main():
     ap.add_argument("--row-stride", type=int, default=64)
     ap.add_argument("--procs", type=int, default=4)
     args = ap.parse_args()
+    if args.workload == "tiny_wire_fp64":
+        tiny_wire(args.workload)
+        return
     p = make_problem(args.workload)
     cols = [int(c) for c in p.cols[:args.ncols]]
     jobs = [(args.workload, j, 1e-10, args.row_stride) for j in cols]

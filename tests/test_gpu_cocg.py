@@ -47,7 +47,8 @@ def relf(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-KINDS = [1, 2]   # RSFD_PASS_RECOMPUTE (fused, three vectors), RSFD_PASS_STORED (five vectors)
+KINDS = [1, 2, 3]   # RSFD_PASS_RECOMPUTE (fused, three vectors), RSFD_PASS_STORED (five vectors), RSFD_PASS_SPLIT
+                    # (the five-vector iteration as a combine launch and a stencil launch)
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -106,7 +107,7 @@ def test_seed_switching_and_policies(rs, pkind):
             assert info["switches"].max() >= 1
 
 
-@pytest.mark.parametrize("prec,kind", [("DF64", 2), ("DF64", 1), ("MIXED", 1), ("MIXED", 2)])
+@pytest.mark.parametrize("prec,kind", [("DF64", 2), ("DF64", 1), ("DF64", 3), ("MIXED", 1), ("MIXED", 2), ("MIXED", 3)])
 def test_launch_modes_bitwise_identical(rs, prec, kind):
     """Graph replay, plain launches, profiled launches and another collapse length all run the same
     fixed-order reductions; the collapse length only regroups exact-order sums of the shift update,
@@ -179,7 +180,7 @@ def test_argument_errors(rs):
             with pytest.raises(rs.RsfdError):
                 rs.rsfd_shifted_cocg(h.ptr, args["cols"], p.energies, args["eta"], args["tol"], 100, G0)
         # launch options the pass cannot honour are rejected before any launch
-        for bad in (dict(pass_kind=3), dict(rows_per_thread=3), dict(prefetch=8), dict(pass_kind=2, tile_y=6,
+        for bad in (dict(pass_kind=4), dict(rows_per_thread=3), dict(prefetch=8), dict(pass_kind=2, tile_y=6,
                                                                                    rows_per_thread=4),
                     dict(pass_kind=2, tile_y=64)):
             with pytest.raises(rs.RsfdError):
@@ -251,3 +252,41 @@ def test_double_float_bench_shape_fourth_order(rs, grid):
     Go, ores = shifted_cocg_columns(p, tol=1e-12)
     assert relf(G, Go) <= 1e-6
     assert max(r.switches for r in ores) >= 1
+
+
+@pytest.mark.parametrize("prec,bound", [("FP64", 1e-9), ("DF64", 1e-6)])
+def test_seed_outside_the_energy_set(rs, prec, bound):
+    """Auxiliary seed energies (the extension of Eq. seedswitch to an energy outside the set): the
+    first seed far below the spectrum, and a switch target inside it, against the oracle run with the
+    same auxiliary energies and against the oracle with an in-set seed."""
+    from oracle.cocg import shifted_cocg
+    from oracle.operator import hamiltonian, apply_h
+    p = small_problem(grid=(12, 10, 14), h=0.5, fd_order=4, n_wells=2, n_energies=5, e_range=(-3.0, -1.0),
+                      eta=5e-2, tol=1e-11, cols=3)
+    H, P, wE = hamiltonian(p)
+    b_rows = boundary_rows(p.grid, p.n_face)
+    Z = p.energies + 1j * p.eta
+    aux = np.array([-12.0, 1.7])
+    cases = [(rs.RSFD_SEED_AUX, 0, ("aux", 0)), (rs.RSFD_SEED_FIRST, 0, "first")]
+    Gref, _ = shifted_cocg_columns(p, tol=1e-12)
+    for kind, idx, oseed in cases:
+        Go = np.zeros((p.K, b_rows.size, p.cols.size), complex)
+        osw = []
+        for jj, j in enumerate(p.cols):
+            b = np.zeros(p.N, complex)
+            b[j] = 1.0
+            r = shifted_cocg(lambda v: apply_h(H, P, wE, v), b, Z, p.tol, rows=b_rows, seed=oseed,
+                             aux=aux + 1j * p.eta)
+            Go[:, :, jj] = r.x
+            osw.append(r.seeds[-1])
+        with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=getattr(rs, "RSFD_" + prec)) as h:
+            G0 = torch.zeros((p.K, p.cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+            st, info, res = rs.rsfd_shifted_cocg(h.ptr, p.cols, p.energies, p.eta, p.tol, p.maxit, G0, kind, idx,
+                                                 aux_energies=aux)
+            torch.cuda.synchronize()
+            G = G0.cpu().numpy().astype(np.complex128).transpose(0, 2, 1)
+        assert st == rs.RSFD_OK and res.shape == (p.cols.size, p.K)
+        # the seed ends on the auxiliary energy inside the spectrum (index K + 1), as in the oracle
+        assert (info["switches"] >= 1).all() and list(info["final_seed"]) == osw == [p.K + 1] * p.cols.size
+        assert relf(G, Go) <= bound
+        assert relf(G, Gref) <= max(bound, 1e-9)

@@ -59,14 +59,22 @@ def test_dyson_random_matrices(rs, nb):
     assert (ref < 1e-12).all()
 
 
-def test_tiny_wire_end_to_end_fp64(rs):
+@pytest.mark.parametrize("prec,kind,tol,gb,tb", [
+    ("FP64", 0, None, 1e-9, 1e-9),
+    # the double-float form the library ships, in the stored and split passes: the stated mixed-mode
+    # tolerances, G_bb relative error <= 1e-5 and |dT| <= 1e-4
+    ("DF64", 2, 1e-9, 1e-5, 1e-4),
+    ("DF64", 3, 1e-9, 1e-5, 1e-4),
+])
+def test_tiny_wire_end_to_end(rs, prec, kind, tol, gb, tb):
     """G0_bb (shifted COCG) -> host Sigma -> Dyson -> T on the 8x8x12 wire, against the dense
     (Z - H - Sigma)^{-1} of the oracle."""
     p = make_problem("tiny_wire_fp64")
     b = boundary_rows(p.grid, p.n_face)
-    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_FP64) as h:
+    with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=getattr(rs, "RSFD_" + prec)) as h:
+        rs.rsfd_set_solve_options(h.ptr, pass_kind=kind)
         G0 = torch.zeros((p.K, h.nb, h.nb), dtype=torch.complex128, device="cuda")
-        st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, p.tol, p.maxit, G0)
+        st, info, res = rs.rsfd_shifted_cocg(h.ptr, h.rows, p.energies, p.eta, tol or p.tol, p.maxit, G0)
         assert st == rs.RSFD_OK
         SLh, SRh = rs.rsfd_lead_sigma_uniform(p.grid[0], p.grid[1], p.h, p.fd_order, p.energies, p.eta)
         SL, SR = torch.from_numpy(SLh).cuda(), torch.from_numpy(SRh).cuda()
@@ -78,9 +86,9 @@ def test_tiny_wire_end_to_end_fp64(rs):
         Z = E + 1j * p.eta
         SLo, SRo = sigma_bloch(p.grid[0], p.grid[1], p.h, p.fd_order, Z)
         Gd = g_dense(p, Z, SLo, SRo, rows=b, cols=b)
-        assert np.linalg.norm(Gg[k] - Gd) / np.linalg.norm(Gd) <= 1e-9
+        assert np.linalg.norm(Gg[k] - Gd) / np.linalg.norm(Gd) <= gb
         To = transmission(Gd, SLo, SRo)[0]
-        assert abs(T[k] - To) <= 1e-9
+        assert abs(T[k] - To) <= tb
         assert -1e-6 <= T[k] <= open_channels(p.grid[0], p.grid[1], p.h, p.fd_order, E) + 1e-2
 
 
@@ -170,3 +178,26 @@ def test_tracked_planes_interior_blocks(rs, prec, bound):
             dos = -np.trace(Gm[k][blk, blk]).imag / np.pi
             dos_o = -np.trace(Gd[blk, blk]).imag / np.pi
             assert dos > 0 and abs(dos - dos_o) <= 10 * bound * abs(dos_o)
+
+
+@pytest.mark.parametrize("prec,kind", [("FP64", 1), ("FP64", 2), ("DF64", 2)])
+def test_dyson_left_slab_columns_for_transmission(rs, prec, kind):
+    """dyson_cols = 1 solves only the left slab's columns of G_bb (the block G_RL that Eq. TF reads):
+    those columns equal the oracle's Dyson solution, the rest are zero, and T is unchanged."""
+    nb, K = 70, 3
+    ns = nb // 2
+    G0 = random_complex_matrices(nb, K, seed=31, scale=0.5)
+    SL = random_complex_matrices(ns, K, seed=32, scale=0.5, imag_sign=-1)
+    SR = random_complex_matrices(ns, K, seed=33, scale=0.5, imag_sign=-1)
+    with rs.Handle((ns, 1, 4), 0.5, 2, np.zeros(ns * 4), n_face=1, precision=getattr(rs, "RSFD_" + prec)) as h:
+        rs.rsfd_set_solve_options(h.ptr, dyson_kind=kind, dyson_cols=1)
+        G = torch.full((K, nb, nb), 3.0, dtype=torch.complex128, device="cuda")
+        ref = rs.rsfd_dyson_boundary(h.ptr, _abi(G0), _abi(SL), _abi(SR), G)
+        Gg = _mat(G)
+        T = rs.rsfd_transmission(h.ptr, G, _abi(SL), _abi(SR))
+    for k in range(K):
+        Go = dyson_solve(G0[k], SL[k], SR[k])
+        assert np.linalg.norm(Gg[k][:, :ns] - Go[:, :ns]) / np.linalg.norm(Go[:, :ns]) <= 1e-10
+        assert np.all(Gg[k][:, ns:] == 0)
+        assert abs(T[k] - transmission(Go, SL[k], SR[k])[0]) <= 1e-9 * max(1.0, abs(T[k]))
+    assert (ref < 1e-12).all()

@@ -78,13 +78,14 @@ def test_projectors_reduced_precision_match_dense(rs, prec, tol, bound):
         assert relf(G[k], Gd) <= bound
 
 
+@pytest.mark.parametrize("kind", [2, 3])
 @pytest.mark.parametrize("grid,slots,tile_y", [((37, 21, 20), 3, 8), ((40, 18, 17), 5, 16)])
-def test_projectors_ragged_tiles_match_oracle(rs, grid, slots, tile_y):
+def test_projectors_ragged_tiles_match_oracle(rs, grid, slots, tile_y, kind):
     """Several x/y tiles with ragged edges, overlapping projector supports, seed switching: the GPU
     iterates equal the oracle's shifted COCG (FP64)."""
     p = small_problem(grid=grid, h=0.5, fd_order=4, n_wells=3, projectors=6, n_energies=5,
                       e_range=(0.5, 2.5), eta=5e-2, tol=1e-11, cols=slots + 2)
-    st, G, info = gpu_g0(rs, p, rs.RSFD_FP64, p.cols, opts=dict(slots=slots, tile_y=tile_y))
+    st, G, info = gpu_g0(rs, p, rs.RSFD_FP64, p.cols, opts=dict(slots=slots, tile_y=tile_y, pass_kind=kind))
     assert st == rs.RSFD_OK
     Go, res = shifted_cocg_columns(p, cols=p.cols, tol=1e-11)
     assert relf(G, Go) <= 1e-9
@@ -101,12 +102,12 @@ def peapod_oracle():
     return p, cols, Go
 
 
-@pytest.mark.parametrize("prec,bound", [("FP64", 1e-10), ("DF64", 1e-6)])
-def test_peapod_full_size_first_iterations_match_oracle(rs, peapod_oracle, prec, bound):
+@pytest.mark.parametrize("prec,bound,kind", [("FP64", 1e-10, 2), ("DF64", 1e-6, 2), ("DF64", 1e-6, 3)])
+def test_peapod_full_size_first_iterations_match_oracle(rs, peapod_oracle, prec, bound, kind):
     """The 72 x 72 x 256 peapod-shaped workload (460 wells + 460 KB projectors, 100 energies): the
     boundary rows of x^(i) after 40 iterations for two sampled columns equal the oracle's."""
     p, cols, Go = peapod_oracle
-    st, G, info = gpu_g0(rs, p, getattr(rs, "RSFD_" + prec), cols, maxit=40)
+    st, G, info = gpu_g0(rs, p, getattr(rs, "RSFD_" + prec), cols, maxit=40, opts=dict(pass_kind=kind))
     assert st == rs.RSFD_ERR_NOT_CONVERGED
     assert (info["iters"] == 40).all()
     assert relf(G, Go) <= bound
