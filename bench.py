@@ -237,7 +237,8 @@ def run_gpu(args):
     vsz = 8 if prec == rs.RSFD_MIXED else 16
     h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, proj=p.proj, precision=prec)
     rs.rsfd_set_solve_options(h.ptr, slots=args.slots, iters_per_sync=args.iters_per_sync, tile_y=args.tile_y,
-                              z_chunk=args.z_chunk, pass_kind=args.pass_kind, prefetch=args.prefetch, profile=1)
+                              z_chunk=args.z_chunk, pass_kind=args.pass_kind, prefetch=args.prefetch, profile=1,
+                              reg_budget=args.reg_budget)
     tuned = None
     if not args.no_autotune:
         # launch options picked by the library's autotuner for this block width (not timed)
@@ -291,7 +292,7 @@ def run_gpu(args):
     N, nb, K = p.N, h.nb, p.K
     # fused pass: read r_{n-1}, r_{n-2}, write r_n per slot-iteration, plus V once per launch
     kind_used = tuned["pass_kind"] if tuned else args.pass_kind
-    launches_per_iter = 2 if kind_used == 3 else 1        # the split pass: combine + stencil launches
+    launches_per_iter = 2 if kind_used in (3, 4) else 1   # the split passes: combine + stencil launches
     iter_launches = agg["n_pass"] / launches_per_iter     # seed iterations launched (all slots at once)
     pass_bytes = agg["slot_iterations"] * (3 * vsz * N) + iter_launches * (vsz // 2) * N
     proj_bytes_per_it = 0
@@ -311,7 +312,7 @@ def run_gpu(args):
     peak, peak_src = _peaks()
     kern = {"pass": (pass_bytes, agg["ms_pass"]), "shift": (shift_bytes, agg["ms_shift"])}
     split = None
-    if kind_used == 3 and agg["ms_combine"] > 0:
+    if kind_used in (3, 4) and agg["ms_combine"] > 0:
         # the split pass's two launches against their own algorithmic bytes: the combine reads r_{n-1},
         # r_{n-2}, A r_{n-1} and writes r_n (4 v N); the stencil reads r_n and writes A r_n (2 v N, plus
         # the potential once per launch and the projector terms)
@@ -805,8 +806,10 @@ def main():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--prefetch", type=int, default=0, help="with --no-autotune: TMA planes in flight (1..7)")
     ap.add_argument("--pass-kind", type=int, default=0,
-                    help="with --no-autotune: 1 fused, 2 stored-product, 3 split (combine + stencil launches)")
+                    help="with --no-autotune: 1 fused, 2 stored-product, 3 split (combine + stencil launches), "
+                         "4 split with block-floating-point leading parts (double-float)")
     ap.add_argument("--z-chunk", type=int, default=0)
+    ap.add_argument("--reg-budget", type=int, default=0, help="with --no-autotune: the pass's register budget option")
     ap.add_argument("--ncols", type=int, default=0, help="use only the first n columns (quick runs)")
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--iters-per-sync", type=int, default=0)

@@ -114,9 +114,18 @@ typedef enum {
                               recomputed on the tile plus halo and A r_n again for the dot products */
   RSFD_PASS_STORED = 2,    /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);
                               one stencil application per grid point */
-  RSFD_PASS_SPLIT = 3      /* the stored-product iteration as two launches: a pointwise combine (r_n from
+  RSFD_PASS_SPLIT = 3,     /* the stored-product iteration as two launches: a pointwise combine (r_n from
                               r_{n-1}, r_{n-2}, A r_{n-1}; four vectors) and a stencil (A r_n from r_n; two
                               vectors plus its halo); one row per thread, tile width 32, tile_y <= 16 */
+  RSFD_PASS_SPLIT_BFP = 4  /* double-float handles without projectors: RSFD_PASS_SPLIT with the leading
+                              parts of r_n rounded to a per-column, per-iteration quantum q (block floating
+                              point, q chosen from a bound on |r_n| so that every leading part is at most
+                              2^21 q) and the product stored as s A r
+                              with s = 24 h^2 (4th order) or 2 h^2 (2nd order), which makes the neighbour
+                              weights the integers 16, -1 (or 1): the stencil's neighbour sums of leading
+                              parts are then exact FP32 additions.  The iterates agree with RSFD_PASS_SPLIT
+                              to double-float rounding (about 2^-45 of the bound on |r_n|);
+                              other handles run RSFD_PASS_SPLIT */
 } rsfd_pass_kind;
 
 /* Form of the Dyson solve (rsfd_solve_opts.dyson_kind). */
@@ -147,7 +156,9 @@ typedef struct {
   int32_t reg_budget;     /* RSFD_PASS_STORED, double-float, one row per thread: registers per thread of
                              the pass, 0 = at most 96 (CTAs of <= 640 threads; two CTAs of <= 320 threads
                              per SM), 1 = at most 128 (CTAs of <= 512 threads, tile_y <= 14, one CTA per
-                             SM, no register spills); other passes ignore it */
+                             SM, no register spills); RSFD_PASS_SPLIT_BFP: the stencil launch keeps 0 = at
+                             most 96 (one 512-thread CTA per SM) or 1 = at most 64 registers (two); other
+                             passes ignore it */
   int32_t tile_x;         /* RSFD_PASS_STORED, double-float, one row per thread: tile width in x, 0 or 32
                              (one tile row per warp) or 16 (two tile rows per warp; less idle work when Nx
                              is an odd multiple of 16, e.g. 48 or 80); tile_y must be even */
@@ -168,7 +179,7 @@ typedef struct {
   double ms_total;            /* wall time of the call on the device stream (events) */
   double ms_pass;             /* summed duration of stencil/seed-update launches (profile = 1) */
   double ms_shift;            /* summed duration of the collapsed shift-update launches (profile = 1) */
-  int64_t n_pass;             /* stencil/seed-update launches (two per iteration for RSFD_PASS_SPLIT) */
+  int64_t n_pass;             /* stencil/seed-update launches (two per iteration for the split passes) */
   int64_t n_shift;            /* collapsed shift-update launches (the apply kernel) */
   int64_t n_other;            /* other kernel launches (collapse coefficients, history reset, projector
                                  terms, slot set-up, write-out) */
@@ -177,7 +188,7 @@ typedef struct {
   int64_t shift_slot_chunks;  /* (column, collapse) pairs: each reads and writes x_b, p_b of K energies once */
   int32_t slots;              /* columns in flight that were used */
   int32_t iters_per_sync;
-  double ms_combine;          /* RSFD_PASS_SPLIT with profile = 1: the combine launches' part of ms_pass */
+  double ms_combine;          /* split passes with profile = 1: the combine launches' part of ms_pass */
 } rsfd_stats;
 
 /* Create a handle for one transition region (Sec. II A, Eq. sabun1).

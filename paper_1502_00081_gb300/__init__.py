@@ -15,7 +15,7 @@ Appendix) and the OBM/Dyson relation to the perturbed ones (Eq. sec3-01a).
 from .binding import (  # noqa: F401
     RSFD_OK, RSFD_ERR_ARG, RSFD_ERR_ALLOC, RSFD_ERR_CUDA, RSFD_ERR_NOT_CONVERGED, RSFD_ERR_BREAKDOWN,
     RSFD_ERR_TIMEOUT, RSFD_ERR_UNSUPPORTED, RSFD_FP64, RSFD_MIXED, RSFD_DF64, RSFD_SEED_MID, RSFD_SEED_FIRST, RSFD_SEED_INDEX, RSFD_SEED_AUX,
-    RSFD_PASS_AUTO, RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED, RSFD_PASS_SPLIT, RSFD_DYSON_AUTO, RSFD_DYSON_FP64, RSFD_DYSON_TC,
+    RSFD_PASS_AUTO, RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED, RSFD_PASS_SPLIT, RSFD_PASS_SPLIT_BFP, RSFD_DYSON_AUTO, RSFD_DYSON_FP64, RSFD_DYSON_TC,
     RsfdError, lib_path, load_library,
     rsfd_create, rsfd_boundary_rows, rsfd_set_tracked_planes, rsfd_tracked_rows, rsfd_dyson_tracked,
     rsfd_set_solve_options, rsfd_shifted_cocg, rsfd_get_stats, rsfd_autotune, rsfd_shifted_cocg_regions, rsfd_shifted_cocg_sweep, rsfd_sweep_load_energies,

@@ -32,6 +32,7 @@ RSFD_PASS_AUTO = 0
 RSFD_PASS_RECOMPUTE = 1
 RSFD_PASS_STORED = 2
 RSFD_PASS_SPLIT = 3
+RSFD_PASS_SPLIT_BFP = 4
 RSFD_DYSON_AUTO = 0
 RSFD_DYSON_FP64 = 1
 RSFD_DYSON_TC = 2

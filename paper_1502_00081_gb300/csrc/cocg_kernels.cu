@@ -350,6 +350,60 @@ template <int R> struct Stencil<RSFD_DF64, R> {
   }
 };
 
+// s A x at one point for the block-floating-point split pass (double-float vectors whose leading
+// parts are multiples of one quantum q, each at most 2^21 q), with s = 24 h^2 (R = 2) or 2 h^2 (R = 1):
+//   s A x = 16 S1 - S2 + d x  (R = 2),   S1 + d x  (R = 1),   d = s (Z_s - hd - V) (complex),
+// S1, S2 the sums of the six neighbours at distance 1 and 2.  The neighbour sums of the leading parts
+// are exact FP32 additions (every partial sum is a multiple of q below 6 * 2^21 q < 2^24 q), 16 S1h
+// is exact and one TwoSum forms 16 S1h - S2h; the trailing parts are summed plainly; d x takes exact
+// products (FMA) and two more TwoSums join the terms.
+template <int R> struct StencilBFP {
+  static __device__ __forceinline__ float2 sum6h(const dfc (&n)[6]) {
+    return f2add(f2add(f2add(n[0].h, n[1].h), f2add(n[2].h, n[3].h)), f2add(n[4].h, n[5].h));
+  }
+  static __device__ __forceinline__ float2 sum6l(const dfc (&n)[6]) {
+    return f2add(f2add(f2add(n[0].l, n[1].l), f2add(n[2].l, n[3].l)), f2add(n[4].l, n[5].l));
+  }
+  // zre = s (Re Z_s - hd), zim = s Im Z_s (double-float scalars), vs = s V at the point
+  static __device__ __forceinline__ dfc applyA(const dfc& c, const dfc (&n1)[6], const dfc (&n2)[6], float2 vs,
+                                               dfr zre, float2 zim_h, float2 zim_l) {
+    // L = 16 S1 - S2 (R = 2) or S1 (R = 1) as a leading part Lh and a trailing part Ll
+    float2 Lh, Ll;
+    if (R == 2) {
+      float2 le;
+      two_sum2(f2mul(bc(16.f), sum6h(n1)), f2neg(sum6h(n2)), Lh, le);
+      Ll = f2sub(f2fma(bc(16.f), sum6l(n1), le), sum6l(n2));
+    } else {
+      Lh = sum6h(n1);
+      Ll = sum6l(n1);
+    }
+    // P1 = dre x, dre = zre - vs (real double-float): p1 - ne1 exactly (up to the lo*lo term)
+    const dfr dre = dfr_sub(zre, vs.x, vs.y);
+    const float2 dh = bc(dre.h), ndh = bc(-dre.h);
+    const float2 p1 = f2mul(dh, c.h);
+    float2 ne1 = f2fma(ndh, c.h, p1);
+    ne1 = f2fma(ndh, c.l, ne1);
+    ne1 = f2fma(bc(-dre.l), c.h, ne1);
+    // P2 = i zim x = zim (-x.im, x.re): zim_h = (-zim.h, zim.h), zim_l = (-zim.l, zim.l)
+    const float2 sh = make_float2(c.h.y, c.h.x), sl = make_float2(c.l.y, c.l.x);
+    const float2 p2 = f2mul(zim_h, sh);
+    float2 ne2 = f2fma(f2neg(zim_h), sh, p2);
+    ne2 = f2fma(f2neg(zim_h), sl, ne2);
+    ne2 = f2fma(f2neg(zim_l), sh, ne2);
+    // u = p1 + p2 +- Lh + (lo terms)
+    float2 s1, t1, s2, t2;
+    two_sum2(p1, p2, s1, t1);
+    two_sum2(s1, Lh, s2, t2);
+    float2 lo = f2add(t1, t2);
+    lo = f2sub(lo, ne1);
+    lo = f2sub(lo, ne2);
+    lo = f2add(lo, Ll);
+    dfc u;
+    fast_two_sum2(s2, lo, u.h, u.l);
+    return u;
+  }
+};
+
 template <class T> struct Pair {
   T a, b;
 };
@@ -633,6 +687,18 @@ __device__ __forceinline__ void block_sum_lane0(double (&v)[NV], double* s_red) 
   }
   __syncthreads();
 }
+// Largest of a non-negative per-thread value over the block, valid in thread 0 (order-free).
+__device__ __forceinline__ float block_max0(float v, float* s_red) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) s_red[wid] = v;
+  __syncthreads();
+  if (tid == 0)
+    for (int w = 0; w < nw; ++w) v = fmaxf(v, s_red[w]);
+  __syncthreads();
+  return v;
+}
 
 struct PassParams {
   SolveDims d;
@@ -658,7 +724,26 @@ struct PassParams {
   int has_proj;              // 1: nonlocal projectors; the pass leaves its dots in pdots and the
                              //    projector kernel finishes A r_n, the dots and the scalar step
   double* pdots;
+  // block-floating-point split pass: the stencil stores u = s A r; the combine multiplies it by
+  // aA / s (aA is stored so) and rounds the leading parts of r_n to the slot's quantum q; partial
+  // entries 5 and 6 carry the largest leading-part components of r_n and of u_n
+  int bfp;
+  int kb;                    // leading parts are at most 2^kb q (21)
+  double uscale;             // s (1 for the other forms)
+  const void* Vs;            // s V, (hi, lo) floats
 };
+
+// Quantum of the block-floating-point leading parts for a bound B on every component of the next
+// r_n: the power of two q with B < 2^kb q (clamped to a normal FP32 range).
+__device__ __forceinline__ double bfp_quantum(double B, int kb) {
+  if (!(B > 0.0) || !(B < 1e300)) return ldexp(1.0, -100);
+  int e;
+  frexp(B * (1.0 + 0x1p-20), &e);   // B (1 + 2^-20) < 2^e
+  int ex = e - kb;
+  if (ex < -100) ex = -100;
+  if (ex > 100) ex = 100;
+  return ldexp(1.0, ex);
+}
 
 // ------------------------------------------------------------------------------------------------
 // FP64 scalar step of one slot (run by the last CTA of the slot)
@@ -667,6 +752,7 @@ struct ScalarShared {
   double2 rr, rAr;
   double nrm2;
   double2 beta, alpha, c, scale_n, scale_nm1, fn, fnm1, Zs;
+  double maxr, maxu;   // block-floating-point split pass: largest leading-part components of r_n, s A r_n
   int stop;
   int do_switch;
   int seed;
@@ -843,7 +929,16 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
     }
     st->a1 = a1;
     st->a2 = cmul(make_double2(-c.x, -c.y), S.scale_nm1);
-    st->aA = cmul(make_double2(-S.alpha.x, -S.alpha.y), S.scale_n);
+    st->aA = cscale(1.0 / p.uscale, cmul(make_double2(-S.alpha.x, -S.alpha.y), S.scale_n));
+    if (p.bfp) {
+      // bound on every component of the next r_n = a1 r_n + a2 r_{n-1} + aA (s A r_n) from the
+      // largest components of the stored vectors (|Re(a x)|, |Im(a x)| <= (|a.x| + |a.y|) max)
+      const double2 a2 = st->a2, aA = st->aA;
+      const double B = (fabs(a1.x) + fabs(a1.y)) * S.maxr + (fabs(a2.x) + fabs(a2.y)) * st->mr_prev +
+                       (fabs(aA.x) + fabs(aA.y)) * S.maxu;
+      st->mr_prev = S.maxr;
+      st->q = bfp_quantum(B, p.kb);
+    }
     st->Zs = S.Zs;
     st->seed = S.seed;
     st->alpha_prev = S.alpha;
@@ -860,13 +955,19 @@ __device__ void scalar_step(const PassParams& p, int slot, ScalarShared& S) {
 // atomic ticket; the last of the slot's ctas_per_slot CTAs sums all npart partials of the slot in
 // order (warp 0, fixed tree; the split pass's combine kernel has left its partials in entries
 // ctas_per_slot ...) and returns true with (r,r), (r,Ar), ||r||^2 in S.  No CTA waits on another.
-__device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)[5], ScalarShared& S, int& s_last) {
+__device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)[5], ScalarShared& S, int& s_last,
+                            float mxu = 0.f) {
   const int tid = threadIdx.x;
   block_sum_lane0<5>(v5, S.red);
+  if (p.bfp) mxu = block_max0(mxu, reinterpret_cast<float*>(S.red));
   if (tid == 0) {
     double* dst = p.partials + ((size_t)slot * p.d.npart + cta) * 8;
 #pragma unroll
     for (int k = 0; k < 5; ++k) dst[k] = v5[k];
+    if (p.bfp) {
+      dst[5] = 0.0;
+      dst[6] = (double)mxu;
+    }
     __threadfence();
     const unsigned int t = atomicAdd(p.tickets + slot, 1u);
     s_last = (t == (unsigned int)(p.d.ctas_per_slot - 1));
@@ -883,10 +984,24 @@ __device__ bool pass_finish(const PassParams& p, int slot, int cta, double (&v5)
     }
 #pragma unroll
     for (int j = 0; j < 5; ++j) w5[j] = warp_sum(w5[j]);
+    double mr = 0.0, mu = 0.0;
+    if (p.bfp) {
+      for (int k = tid; k < p.d.npart; k += 32) {
+        mr = fmax(mr, __ldcg(src + (size_t)k * 8 + 5));
+        mu = fmax(mu, __ldcg(src + (size_t)k * 8 + 6));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+        mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+      }
+    }
     if (tid == 0) {
       S.rr = make_double2(w5[0], w5[1]);
-      S.rAr = make_double2(w5[2], w5[3]);
+      // the block-floating-point split pass sums (r, s A r)
+      S.rAr = p.uscale != 1.0 ? cscale(1.0 / p.uscale, make_double2(w5[2], w5[3])) : make_double2(w5[2], w5[3]);
       S.nrm2 = w5[4];
+      S.maxr = mr;
+      S.maxu = mu;
       p.tickets[slot] = 0u;
     }
   }
@@ -1510,16 +1625,35 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
 // step so that six 16-byte loads are in flight.
 constexpr int kCombThreads = 256;
 
-template <int MODE>
-__global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
+// Block-floating-point rounding of the leading parts (BFP): with Cq = 1.5 2^23 q, fl(h + Cq) - Cq is h
+// rounded to a multiple of q (exact while |h| < 2^22 q: h + Cq stays in Cq's binade, whose spacing
+// is q), and h - hq is exact; the remainder joins the trailing part.
+template <bool BFP, typename C> struct Requant {
+  static __device__ __forceinline__ C apply(const C& x, float2) { return x; }
+  static __device__ __forceinline__ float amax(const C&) { return 0.f; }
+};
+template <> struct Requant<true, dfc> {
+  static __device__ __forceinline__ dfc apply(const dfc& x, float2 cq) {
+    dfc r;
+    r.h = f2sub(f2add(x.h, cq), cq);
+    r.l = f2add(x.l, f2sub(x.h, r.h));
+    return r;
+  }
+  static __device__ __forceinline__ float amax(const dfc& x) { return fmaxf(fabsf(x.h.x), fabsf(x.h.y)); }
+};
+
+// one combine CTA: block cblk (of d.ctas_c, a range of z-planes) of slot `slot`; any block size
+template <int MODE, bool BFP>
+__device__ __forceinline__ void combine_body(const PassParams& p, const int slot, const int cblk) {
   typedef Ops<MODE> O;
   typedef Stencil<MODE, 1> ST;   // combine() does not depend on the stencil reach
   typedef typename O::C C;
   typedef typename O::H H;
+  typedef Requant<BFP, C> RQ;
   __shared__ double s_red[32 * 5];
   __shared__ typename O::Cplx s_a[3];
   __shared__ int s_n, s_hc;
-  const int slot = blockIdx.y;
+  __shared__ float s_cq;
   const SlotState* st = p.slots + slot;
   if (st->status != SLOT_RUNNING) return;
   const SolveDims& d = p.d;
@@ -1529,9 +1663,12 @@ __global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
     s_a[2] = O::cplx(st->aA);
     s_n = st->n;
     s_hc = st->hcnt;
+    s_cq = BFP ? (float)(1.5 * 8388608.0 * st->q) : 0.f;
   }
   __syncthreads();
   const typename O::Cplx a1 = s_a[0], a2 = s_a[1], aA = s_a[2];
+  const float2 cq = make_float2(s_cq, s_cq);
+  float mxr = 0.f;
   const int n = s_n;
   const int i1 = (n + 2) % 3, i2 = (n + 1) % 3, io = n % 3, iu1 = 3 + (n + 1) % 2;
   const long long pe = (long long)d.nxp * d.ny;   // padded elements per plane
@@ -1542,18 +1679,19 @@ __global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
   C* RO = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + io) * vec;
   H* hist = reinterpret_cast<H*>(p.rhist) + ((size_t)slot * p.hist_len + s_hc) * d.nb;
   const long long nxy = (long long)d.nx * d.ny;
-  const int za = (int)((long long)blockIdx.x * d.nz / gridDim.x);
-  const int zb = (int)((long long)(blockIdx.x + 1) * d.nz / gridDim.x);
+  const int za = (int)((long long)cblk * d.nz / d.ctas_c);
+  const int zb = (int)((long long)(cblk + 1) * d.nz / d.ctas_c);
   const int tid = threadIdx.x;
-  const int dx = kCombThreads % d.nxp, dy = kCombThreads / d.nxp;
+  const int nthr = blockDim.x;
+  const int dx = nthr % d.nxp, dy = nthr / d.nxp;
   typename AccOf<MODE>::type acc;
   for (int z = za; z < zb; ++z) {
     const long long zo = (long long)z * pe;
     const int pl = recorded_plane(d, z);
     int x = tid % d.nxp, y = tid / d.nxp;
-    for (long long e = tid; e < pe; e += 2 * kCombThreads) {
-      // two elements: e and e + 256 (the second may lie past the plane)
-      const long long e2 = e + kCombThreads;
+    for (long long e = tid; e < pe; e += 2 * nthr) {
+      // two elements: e and e + nthr (the second may lie past the plane)
+      const long long e2 = e + nthr;
       int x2 = x + dx, y2 = y + dy;
       if (x2 >= d.nxp) { x2 -= d.nxp; ++y2; }
       const bool has2 = e2 < pe;
@@ -1561,16 +1699,20 @@ __global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
       C r1b = O::zero(), r2b = O::zero(), ub = O::zero();
       if (has2) { r1b = R1[zo + e2]; r2b = R2[zo + e2]; ub = U1[zo + e2]; }
       const C ra = ST::combine(a1, r1a, a2, r2a, aA, ua);   // Eq. rvec
-      RO[zo + e] = ra;
+      const C qa = RQ::apply(ra, cq);
+      RO[zo + e] = qa;
       if (x < d.nx) {
         acc.add_r(ra);
+        if (BFP) mxr = fmaxf(mxr, RQ::amax(qa));
         if (pl >= 0) hist[(size_t)pl * nxy + (size_t)y * d.nx + x] = O::hi(ra);
       }
       if (has2) {
         const C rb = ST::combine(a1, r1b, a2, r2b, aA, ub);
-        RO[zo + e2] = rb;
+        const C qb = RQ::apply(rb, cq);
+        RO[zo + e2] = qb;
         if (x2 < d.nx) {
           acc.add_r(rb);
+          if (BFP) mxr = fmaxf(mxr, RQ::amax(qb));
           if (pl >= 0) hist[(size_t)pl * nxy + (size_t)y2 * d.nx + x2] = O::hi(rb);
         }
       }
@@ -1582,11 +1724,21 @@ __global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
   double v5[5];
   acc.get(v5);
   block_sum_lane0<5>(v5, s_red);
+  if (BFP) mxr = block_max0(mxr, reinterpret_cast<float*>(s_red));
   if (tid == 0) {
-    double* dst = p.partials + ((size_t)slot * d.npart + d.ctas_per_slot + blockIdx.x) * 8;
+    double* dst = p.partials + ((size_t)slot * d.npart + d.ctas_per_slot + cblk) * 8;
 #pragma unroll
     for (int k = 0; k < 5; ++k) dst[k] = v5[k];
+    if (BFP) {
+      dst[5] = (double)mxr;
+      dst[6] = 0.0;
+    }
   }
+}
+
+template <int MODE, bool BFP>
+__global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
+  combine_body<MODE, BFP>(p, blockIdx.y, blockIdx.x);
 }
 
 // Stencil: CTA = a 32 x TY tile of one slot and a z-range, one thread per tile point (one warp per
@@ -1600,9 +1752,13 @@ constexpr int kMaxStagesS = kMaxDepth + 3;
 // CTA-wide barrier per plane: every stage has a "full" mbarrier (the TMA transaction count) and an
 // "empty" one on which each warp arrives once it is done with the stage; thread 0 waits for a stage
 // to be empty before it refills it, so warps run up to the prefetch depth apart.
-template <int MODE, int R, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR,
-                                                             const __grid_constant__ CUtensorMap tmV) {
+// BFP (double-float handles): the r_n it reads has block-floating-point leading parts, tmV maps s V,
+// and it stores u_n = s A r_n (StencilBFP) with the largest leading-part component of u_n.
+// one stencil CTA: tile cta (of d.ctas_per_slot) of slot `slot`; blockDim = 32 x tile_y
+template <int MODE, int R, bool BFP>
+__device__ __forceinline__ void stencil_body(const PassParams& p, const CUtensorMap& tmR, const CUtensorMap& tmV,
+                                             const int slot, const int cta) {
+  static_assert(!BFP || MODE == RSFD_DF64, "the block-floating-point pass is double-float only");
   typedef Ops<MODE> O;
   typedef typename O::C C;
   typedef typename O::VT VT;
@@ -1615,7 +1771,6 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
   __shared__ __align__(8) unsigned long long bars[kMaxStagesS];     // full: TMA bytes landed
   __shared__ __align__(8) unsigned long long ebars[kMaxStagesS];    // empty: every warp done with it
 
-  const int slot = blockIdx.y;
   SlotState* st = p.slots + slot;
   if (st->status != SLOT_RUNNING) return;
   const SolveDims& d = p.d;
@@ -1624,7 +1779,6 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
   const int TY = d.tile_y;
   const int EY = TY + 2 * R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int cta = blockIdx.x;
   const int tz = cta % d.nzchunks;
   const int txy = cta / d.nzchunks;
   const int tx = txy % d.tiles_x, ty = txy / d.tiles_x;
@@ -1650,8 +1804,10 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
   __shared__ Coefs sc;
   if (tid == 0) {
     const double2 Zs0 = st->Zs;
-    sc.zre = O::real(Zs0.x - p.hd);
-    sc.zim = O::real(Zs0.y);
+    // BFP: the diagonal of s A is s (Z_s - hd) - s V
+    const double sd = BFP ? p.uscale : 1.0;
+    sc.zre = O::real(sd * (Zs0.x - p.hd));
+    sc.zim = O::real(sd * Zs0.y);
     sc.mh1 = O::real(-p.hk1);
     sc.mh2 = O::real(-p.hk2);
     sc.n = st->n;
@@ -1662,6 +1818,7 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
   const long long vec = (long long)d.nz * plane_elems;
   C* uout = reinterpret_cast<C*>(p.rbuf) + ((size_t)slot * 5 + iuo) * vec;
   const typename O::Real zre = sc.zre, zim = sc.zim, mh1 = sc.mh1, mh2 = sc.mh2;
+  float mxu = 0.f;
 
   constexpr int mR = (MODE == RSFD_DF64) ? 4 : 2;
   constexpr int mV = (MODE == RSFD_DF64) ? 2 : 1;
@@ -1777,9 +1934,19 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
     if (own) {
       const C rc = zq[CC];
       const VT v = vring[(size_t)ist * PV + ov];
-      const C u = Stencil<MODE, R>::applyA(rc, n1, n2, v, zre, zim, mh1, mh2);
-      acc.add_ra(rc, u);
-      uout[(long long)c * plane_elems + (long long)gy * d.nxp + gx] = u;
+      if constexpr (BFP) {
+        const float2 zh = make_float2(-zim.h, zim.h), zl = make_float2(-zim.l, zim.l);
+        const dfc u = StencilBFP<R>::applyA(rc, n1, n2, v, zre, zh, zl);
+        dfc rn;   // normalised r_n for the exact products of the dot
+        fast_two_sum2(rc.h, rc.l, rn.h, rn.l);
+        acc.add_ra(rn, u);
+        mxu = fmaxf(mxu, fmaxf(fabsf(u.h.x), fabsf(u.h.y)));
+        uout[(long long)c * plane_elems + (long long)gy * d.nxp + gx] = u;
+      } else {
+        const C u = Stencil<MODE, R>::applyA(rc, n1, n2, v, zre, zim, mh1, mh2);
+        acc.add_ra(rc, u);
+        uout[(long long)c * plane_elems + (long long)gy * d.nxp + gx] = u;
+      }
     }
     ok = end_step();
   };
@@ -1805,7 +1972,7 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
   }
   double v5[5];
   acc.get(v5);
-  if (pass_finish(p, slot, cta, v5, S, s_last)) {
+  if (pass_finish(p, slot, cta, v5, S, s_last, mxu)) {
     if (p.has_proj) {
       if (tid == 0) {
         double* o = p.pdots + (size_t)slot * 8;
@@ -1819,6 +1986,12 @@ __global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const _
       scalar_step(p, slot, S);
     }
   }
+}
+
+template <int MODE, int R, int NT, int MINB, bool BFP = false>
+__global__ void __launch_bounds__(NT, MINB) stencil_kernel(PassParams p, const __grid_constant__ CUtensorMap tmR,
+                                                             const __grid_constant__ CUtensorMap tmV) {
+  stencil_body<MODE, R, BFP>(p, tmR, tmV, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -2121,6 +2294,7 @@ struct InitParams {
   const int* init_list;
   const long long* init_grid;
   int seed0;
+  int kb;   // block-floating-point bound exponent of the pass (21)
 };
 
 template <int MODE>
@@ -2188,6 +2362,8 @@ __global__ void __launch_bounds__(256) init_kernel(InitParams p) {
     s.alpha_prev = make_double2(1.0, 0.0);   // alpha_{-1} = 1
     s.rr_prev = make_double2(1.0, 0.0);
     s.carry = make_double2(1.0, 0.0);
+    s.q = bfp_quantum(1.0, p.kb);   // r_0 = e_j: every component at most 1
+    s.mr_prev = 1.0;
     p.slots[slot] = s;
   }
 }
@@ -2215,10 +2391,8 @@ __global__ void writeout_kernel(SolveDims d, const void* xbuf, void* G0, const i
 }
 
 template <int MODE, int R>
-cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
-                          int hist_len, cudaStream_t st, cudaEvent_t mid, bool mid_external) {
-  typedef typename Ops<MODE>::C C;
-  typedef typename Ops<MODE>::VT VT;
+PassParams pass_params(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
+                       int hist_len) {
   PassParams p;
   p.d = d;
   p.rbuf = b.rbuf;
@@ -2239,12 +2413,30 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.maxit = maxit;
   p.hist_len = hist_len;
   p.depth = d.depth;
-  p.stored_u = d.kind == RSFD_PASS_STORED || d.kind == RSFD_PASS_SPLIT;
+  p.stored_u = d.kind == RSFD_PASS_STORED || d.kind == RSFD_PASS_SPLIT || d.kind == RSFD_PASS_SPLIT_BFP;
   p.has_proj = b.n_atoms > 0;
   p.pdots = b.pdots;
+  const bool bfp = MODE == RSFD_DF64 && d.kind == RSFD_PASS_SPLIT_BFP;
+  p.bfp = bfp ? 1 : 0;
+  p.kb = 21;
+  p.uscale = bfp ? b.uscale : 1.0;
+  p.Vs = b.Vs;
+  return p;
+}
+
+template <int MODE, int R>
+cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const StencilCoef& c, double tol, int maxit,
+                          int hist_len, cudaStream_t st, cudaEvent_t mid, bool mid_external) {
+  PassParams p = pass_params<MODE, R>(d, b, c, tol, maxit, hist_len);
+  const bool bfp = p.bfp != 0;
   dim3 grid(d.ctas_per_slot, d.W);
-  if (d.kind == RSFD_PASS_SPLIT) {
-    combine_kernel<MODE><<<dim3(d.ctas_c, d.W), kCombThreads, 0, st>>>(p);
+  if (d.kind == RSFD_PASS_SPLIT || d.kind == RSFD_PASS_SPLIT_BFP) {
+    if constexpr (MODE == RSFD_DF64) {
+      if (bfp) combine_kernel<MODE, true><<<dim3(d.ctas_c, d.W), kCombThreads, 0, st>>>(p);
+      else combine_kernel<MODE, false><<<dim3(d.ctas_c, d.W), kCombThreads, 0, st>>>(p);
+    } else {
+      combine_kernel<MODE, false><<<dim3(d.ctas_c, d.W), kCombThreads, 0, st>>>(p);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mid) {   // profiling: the boundary between the combine and the stencil launch
@@ -2253,6 +2445,19 @@ cudaError_t launch_pass_t(const SolveDims& d, const SolverBuffers& b, const Sten
     }
     const size_t smem = split_smem(MODE, R, d.tile_y, d.depth);
     const int thr = split_threads(d.tile_y);
+    if constexpr (MODE == RSFD_DF64) {
+      if (bfp) {
+        // register budget 1: at most 64 registers, two 512-thread (four 256-thread) CTAs per SM
+        if (d.regs == 1) {
+          if (thr <= 256) stencil_kernel<MODE, R, 256, 4, true><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmVs);
+          else stencil_kernel<MODE, R, 512, 2, true><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmVs);
+        } else {
+          if (thr <= 256) stencil_kernel<MODE, R, 256, 3, true><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmVs);
+          else stencil_kernel<MODE, R, 512, 1, true><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmVs);
+        }
+        return cudaGetLastError();
+      }
+    }
     if (thr <= 256) stencil_kernel<MODE, R, 256, 3><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmV);
     else stencil_kernel<MODE, R, 512, 1><<<grid, thr, smem, st>>>(p, *b.tmR, *b.tmV);
     return cudaGetLastError();
@@ -2351,6 +2556,14 @@ cudaError_t kernels_init() {
   RSFD_ATTR_S(RSFD_DF64, 1)
   RSFD_ATTR_S(RSFD_DF64, 2)
 #undef RSFD_ATTR_S
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 1, 256, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 1, 512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 2, 256, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 2, 512, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 1, 256, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 1, 512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 2, 256, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<RSFD_DF64, 2, 512, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(chunk_apply_kernel<RSFD_DF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -2408,6 +2621,10 @@ cudaError_t launch_proj_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.depth = d.depth;
   p.stored_u = 1;
   p.has_proj = 1;
+  p.bfp = 0;   // the block-floating-point form has no projector term
+  p.kb = 21;
+  p.uscale = 1.0;
+  p.Vs = nullptr;
   p.pdots = b.pdots;
   q.n_atoms = b.n_atoms;
   q.n_supp = b.n_supp;
@@ -2489,6 +2706,7 @@ cudaError_t launch_slot_init(int prec, const SolveDims& d, const SolverBuffers& 
   p.init_list = b.init_list;
   p.init_grid = b.init_grid;
   p.seed0 = seed0;
+  p.kb = 21;
   const long long vec = (long long)d.nz * d.ny * d.nxp;
   long long work = vec > (long long)d.K * d.nb ? vec : (long long)d.K * d.nb;
   int gx = (int)((work + 255) / 256);

@@ -48,6 +48,8 @@ struct Handle {
   std::vector<int> track;      // tracked interior planes (rows recorded after b)
   int nr = 0;                  // recorded rows: nb + track.size() * Nx * Ny
   void* dV = nullptr;
+  void* dVs = nullptr;         // double-float handles: s V for the block-floating-point split pass
+  double uscale = 1.0;         // s = 24 h^2 (4th order) or 2 h^2 (2nd order)
   int64_t* dbrow = nullptr;
   // nonlocal projectors: atom-major and point-major CSR of the same entries on the device
   int n_atoms = 0, n_supp = 0;
@@ -65,10 +67,12 @@ struct Handle {
   DevBuf rbuf, xbuf, pbuf, rhist, coef, eflag, slots, shifts, partials, tickets, Z, init_list, init_grid, counters;
   DevBuf pw, pcorr, pdots, ptickets;   // projector term of the solve
   DevBuf cw, ce;                       // collapse weights and factors of the shift update
-  CUtensorMap tmR, tmV;
+  CUtensorMap tmR, tmV, tmVs;
   // dyson / transmission workspace
   DevBuf dy[8];
 };
+
+static bool is_split(int kind) { return kind == RSFD_PASS_SPLIT || kind == RSFD_PASS_SPLIT_BFP; }
 
 rsfd_status fail(Handle* h, rsfd_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -154,6 +158,7 @@ static void free_all(Handle* h) {
     b.bytes = 0;
   }
   if (h->dV) cudaFree(h->dV);
+  if (h->dVs) cudaFree(h->dVs);
   if (h->dbrow) cudaFree(h->dbrow);
   void* pj[] = {h->d_aptr, h->d_tptr, h->d_tatom, h->d_aidx, h->d_tpidx, h->d_aval, h->d_tval, h->d_aE};
   for (void* q : pj)
@@ -163,6 +168,7 @@ static void free_all(Handle* h) {
   h->d_aval = h->d_tval = nullptr;
   h->d_aE = nullptr;
   h->dV = nullptr;
+  h->dVs = nullptr;
   h->dbrow = nullptr;
 }
 
@@ -207,7 +213,7 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
   const CUtensorMapDataType dt = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const cuuint64_t es = f64 ? 8 : 4;
   const cuuint64_t mR = h->prec == RSFD_DF64 ? 4 : 2, mV = h->prec == RSFD_DF64 ? 2 : 1;
-  const bool stored = kind == RSFD_PASS_STORED || kind == RSFD_PASS_SPLIT;
+  const bool stored = kind == RSFD_PASS_STORED || is_split(kind);
   const cuuint64_t nvec = stored ? 5 : 3;
   const cuuint32_t EY = (cuuint32_t)(tile_y + (stored ? 2 : 4) * h->R);
   const cuuint32_t BX = (cuuint32_t)(stored ? passu_box_x(tile_x) : pass_box_x());
@@ -230,17 +236,26 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
     CUresult r = enc(&h->tmV, dt, 3, h->dV, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled (potential) failed: " + std::to_string((int)r));
+    if (h->dVs) {   // the scaled potential s V: same layout, box and element type
+      r = enc(&h->tmVs, dt, 3, h->dVs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(h, RSFD_ERR_CUDA, "cuTensorMapEncodeTiled (scaled potential) failed: " + std::to_string((int)r));
+    }
   }
   return RSFD_OK;
 }
 
-static int resolve_kind(int, int opt) {
+// the block-floating-point split pass serves double-float handles without projectors; the others
+// run the plain split pass
+static int resolve_kind(int prec, int opt, int n_atoms = 0) {
+  if (opt == RSFD_PASS_SPLIT_BFP) return (prec == RSFD_DF64 && n_atoms == 0) ? opt : RSFD_PASS_SPLIT;
   if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED || opt == RSFD_PASS_SPLIT) return opt;
   return RSFD_PASS_STORED;
 }
 
 static size_t kind_smem(int prec, int R, int tile_y, int depth, int kind, int tile_x = 32) {
-  if (kind == RSFD_PASS_SPLIT) return split_smem(prec, R, tile_y, depth);
+  if (is_split(kind)) return split_smem(prec, R, tile_y, depth);
   return kind == RSFD_PASS_STORED ? passu_smem(prec, R, tile_y, depth, tile_x) : pass_smem(prec, R, tile_y, depth);
 }
 
@@ -251,7 +266,7 @@ static int resolve_rows(int opt) {
 
 static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget = 0, int tile_x = 32) {
   if (tile_y < 1) return false;
-  if (kind == RSFD_PASS_SPLIT) {
+  if (is_split(kind)) {
     // one row per thread, 32-wide tiles, at most 16 rows (512 threads)
     if (tile_x != 32 || rows != 1 || tile_y > 16) return false;
     return split_smem(prec, R, tile_y, 1) <= (size_t)(216 * 1024);
@@ -277,7 +292,7 @@ static bool tile_ok(int prec, int R, int tile_y, int kind, int rows, int budget 
 // the taller tile).  Stored-product pass: 8 rows (measured fastest on the 64 x 64 x 128 workload for
 // both precisions: more CTAs per SM outweigh the larger frame), fewer on smaller grids.
 static int default_tile_y(int prec, int R, int ny, int kind, int rows) {
-  if (kind == RSFD_PASS_SPLIT) return std::max(1, std::min(8, ny));
+  if (is_split(kind)) return std::max(1, std::min(8, ny));
   if (kind == RSFD_PASS_STORED) {
     const int ty = std::max(rows, std::min(8, (ny + rows - 1) / rows * rows));
     if (tile_ok(prec, R, ty, kind, rows)) return ty;
@@ -411,6 +426,23 @@ static rsfd_status rsfd_create_impl(rsfd_handle* out, const int32_t grid[3], dou
           }
         }
     e = cudaMemcpy(h->dV, vh.data(), npad * vsz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && precision == RSFD_DF64) {
+      // s V for the block-floating-point split pass: s = 1 / H's coupling at distance R, which makes
+      // the neighbour weights of s H the integers -16, 1 (4th order) or -1 (2nd order)
+      h->uscale = (fd_order == 4 ? 24.0 : 2.0) * hh * hh;
+      std::vector<unsigned char> vs(npad * vsz, 0);
+      for (long long z = 0; z < h->nz; ++z)
+        for (long long y = 0; y < h->ny; ++y)
+          for (long long x = 0; x < h->nx; ++x) {
+            const double v = h->uscale * V_loc[(z * h->ny + y) * h->nx + x];
+            const long long q = (z * h->ny + y) * h->nxp + x;
+            const float hi = (float)v;
+            ((float*)vs.data())[2 * q] = hi;
+            ((float*)vs.data())[2 * q + 1] = (float)(v - (double)hi);
+          }
+      e = cudaMalloc(&h->dVs, npad * vsz);
+      if (e == cudaSuccess) e = cudaMemcpy(h->dVs, vs.data(), npad * vsz, cudaMemcpyHostToDevice);
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpy(h->dbrow, h->brow.data(), h->nb * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
@@ -549,7 +581,7 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
   }
   if (o->slots < 0 || o->iters_per_sync < 0 || o->tile_y < 0 || o->z_chunk < 0 || o->prefetch < 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: negative option");
-  if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_SPLIT)
+  if (o->pass_kind < 0 || o->pass_kind > RSFD_PASS_SPLIT_BFP)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: bad pass_kind");
   if (o->pass_kind == RSFD_PASS_RECOMPUTE && h->n_atoms > 0)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: the recompute pass has no projector term; use the stored pass");
@@ -558,7 +590,7 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
   const int rows = resolve_rows(o->rows_per_thread);
   if (o->prefetch > pass_max_depth())
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch must be <= " + std::to_string(pass_max_depth()));
-  const int kind = resolve_kind(h->prec, o->pass_kind);
+  const int kind = resolve_kind(h->prec, o->pass_kind, h->n_atoms);
   if (o->reg_budget < 0 || o->reg_budget > 1)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: reg_budget must be 0 or 1");
   if (o->tile_x != 0 && o->tile_x != 16 && o->tile_x != 32)
@@ -647,14 +679,15 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   d.K = K;
   d.kreq = Kout;
   d.ncols = ncols;
-  d.kind = resolve_kind(prec, h->opts.pass_kind);
+  d.kind = resolve_kind(prec, h->opts.pass_kind, h->n_atoms);
   // the projector term follows a pass that stores A r (stored-product or split)
   if (h->n_atoms > 0 && d.kind == RSFD_PASS_RECOMPUTE) d.kind = RSFD_PASS_STORED;
   d.nvec = d.kind == RSFD_PASS_RECOMPUTE ? 3 : 5;
-  if (d.kind == RSFD_PASS_SPLIT) d.rows = 1;
-  d.rows = resolve_rows(h->opts.rows_per_thread);
+  d.rows = is_split(d.kind) ? 1 : resolve_rows(h->opts.rows_per_thread);
   d.tile_y = h->opts.tile_y > 0 ? h->opts.tile_y : default_tile_y(prec, h->R, h->ny, d.kind, d.rows);
-  d.regs = (prec == RSFD_DF64 && d.rows == 1 && d.kind == RSFD_PASS_STORED) ? h->opts.reg_budget : 0;
+  d.regs = (prec == RSFD_DF64 && d.rows == 1 && (d.kind == RSFD_PASS_STORED || d.kind == RSFD_PASS_SPLIT_BFP))
+               ? h->opts.reg_budget
+               : 0;
   d.tile_x = (h->opts.tile_x == 16 && d.kind == RSFD_PASS_STORED) ? 16 : 32;
   d.wait_cap = h->opts.wait_cap;
   d.brk_tol = h->opts.breakdown_tol > 0.0 ? h->opts.breakdown_tol : 1e-28;
@@ -666,7 +699,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     d.depth = h->opts.prefetch;
   } else {
     d.depth = 1;
-    const int dmax = d.kind == RSFD_PASS_STORED ? 3 : (d.kind == RSFD_PASS_SPLIT ? 4 : pass_max_depth());
+    const int dmax = d.kind == RSFD_PASS_STORED ? 3 : (is_split(d.kind) ? 4 : pass_max_depth());
     for (int dp = dmax; dp >= 1; --dp)
       if (kind_smem(prec, h->R, d.tile_y, dp, d.kind, d.tile_x) <= (size_t)(216 * 1024)) {
         d.depth = dp;
@@ -712,7 +745,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     }
   }
   d.W = W;
-  if (d.kind == RSFD_PASS_SPLIT) {
+  if (is_split(d.kind)) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     d.ctas_c = split_combine_ctas(h->nz, W, sms);
@@ -752,6 +785,9 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   b.tmR = &h->tmR;
   b.tmV = &h->tmV;
   b.V = h->dV;
+  b.tmVs = &h->tmVs;
+  b.Vs = h->dVs;
+  b.uscale = h->uscale;
   b.slots = (SlotState*)h->slots.p;
   b.shifts = (ShiftState*)h->shifts.p;
   b.partials = (double*)h->partials.p;
@@ -881,7 +917,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
       }
     }
   } gr;
-  const bool split_ev = h->opts.profile && d.kind == RSFD_PASS_SPLIT;
+  const bool split_ev = h->opts.profile && is_split(d.kind);
   if (h->opts.profile) {
     for (int i = 0; i < 2; ++i) {
       gr.ev[i].resize(C + 2 + (split_ev ? C : 0));   // [C + 2 + t]: between the split pass's two launches
@@ -928,7 +964,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
       rsfd_status cs = issue_chunk(par);
       if (cs != RSFD_OK) return cs;
     }
-    h->stats.n_pass += (int64_t)C * (d.kind == RSFD_PASS_SPLIT ? 2 : 1);   // the split pass launches twice
+    h->stats.n_pass += (int64_t)C * (is_split(d.kind) ? 2 : 1);   // the split passes launch twice per iteration
     h->stats.n_shift += 1;
     h->stats.n_other += 2 + (b.n_atoms > 0 ? 2 * C : 0);   // collapse coefficients, history reset, projectors
     RSFD_CK(h, cudaMemcpyAsync(states_of(par), b.slots, W * sizeof(SlotState), cudaMemcpyDeviceToHost, st));
@@ -1131,10 +1167,11 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
   std::vector<rsfd_col_info> info(ncols);
   std::vector<double> res((size_t)ncols * K);
   std::vector<rsfd_solve_opts> cand;
-  const int kinds[3] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE, RSFD_PASS_SPLIT};
+  const int kinds[4] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE, RSFD_PASS_SPLIT, RSFD_PASS_SPLIT_BFP};
   const int zcs[3] = {0, h->nz, (h->nz + 1) / 2};
   for (int kind : kinds) {
-    if (kind == RSFD_PASS_SPLIT) {
+    if (kind == RSFD_PASS_SPLIT_BFP && resolve_kind(h->prec, kind, h->n_atoms) != kind) continue;
+    if (is_split(kind)) {
       // the split pass: tile height and z-chunk
       const int tys[3] = {8, 4, 16};
       const int pfs[2] = {0, 3};
@@ -1142,14 +1179,15 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
         if (ty > h->ny && ty != 4) continue;
         if (!tile_ok(h->prec, h->R, ty, kind, 1)) continue;
         for (int zc : zcs)
-        for (int pf : pfs) {
+        for (int pf : pfs)
+        for (int rb = 0; rb < (kind == RSFD_PASS_SPLIT_BFP ? 2 : 1); ++rb) {
           if (zc > 0 && zc < 8) continue;
           rsfd_solve_opts o = keep;
           o.pass_kind = kind;
           o.rows_per_thread = 0;
           o.tile_y = ty;
           o.z_chunk = zc;
-          o.reg_budget = 0;
+          o.reg_budget = rb;
           o.tile_x = 0;
           o.slots = ncols;
           o.iters_per_sync = C;
@@ -1219,7 +1257,7 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
   }
   best_o.profile = keep.profile;
   best_o.use_graphs = keep.use_graphs;
-  if (best_o.pass_kind != RSFD_PASS_SPLIT) best_o.prefetch = keep.prefetch;   // the split pass tunes its depth
+  if (!is_split(best_o.pass_kind)) best_o.prefetch = keep.prefetch;   // the split pass tunes its depth
   h->opts = best_o;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -79,6 +79,11 @@ struct __align__(16) SlotState {
   double2 alpha_prev; // alpha_{n-1}
   double2 rr_prev;    // (r_{n-1}, r_{n-1}) in the current seed's normalisation
   double2 carry;      // factor that brings the stored r_{n-1} to the current seed's normalisation
+  // block-floating-point split pass (RSFD_PASS_SPLIT_BFP): the next combine rounds the leading
+  // parts of r_n to multiples of q; mr_prev is the largest leading-part component of the stored
+  // r_{n-1} (the r_{n-2} of the next combine)
+  double q;
+  double mr_prev;
 };
 
 // Per (slot, energy) scalars (FP64).
@@ -120,7 +125,7 @@ struct SolveDims {
   int ncols;
   int ntrack;         // interior planes recorded after the boundary planes
   int track[16];      // their z indices (rows 2 nface Nx Ny + e Nx Ny ...)
-  int kind;           // RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED or RSFD_PASS_SPLIT
+  int kind;           // RSFD_PASS_RECOMPUTE, RSFD_PASS_STORED, RSFD_PASS_SPLIT or RSFD_PASS_SPLIT_BFP
   int nvec;           // Krylov vectors per slot in rbuf: 3 (r ring) or 5 (r ring + A r pair)
   int rows;           // stored-product pass: tile rows per thread (1, 2 or 4)
   int regs;           // register budget of the one-row double-float pass (0, 1)
@@ -144,6 +149,9 @@ struct SolverBuffers {
   int* error_flag;        // set by a kernel whose bounded wait expired
   const CUtensorMap* tmR; // TMA map of rbuf
   const CUtensorMap* tmV; // TMA map of the potential
+  const CUtensorMap* tmVs;// TMA map of the scaled potential s V (double-float handles)
+  const void* Vs;         // [Nz][Ny][Nxp] s V as (hi, lo) floats (double-float handles)
+  double uscale;          // s: the block-floating-point split pass stores s A r (integer neighbour weights)
   SlotState* slots;       // [W]
   ShiftState* shifts;     // [W][K]
   double* partials;       // [W][ctas_per_slot][8]

@@ -180,7 +180,7 @@ def test_argument_errors(rs):
             with pytest.raises(rs.RsfdError):
                 rs.rsfd_shifted_cocg(h.ptr, args["cols"], p.energies, args["eta"], args["tol"], 100, G0)
         # launch options the pass cannot honour are rejected before any launch
-        for bad in (dict(pass_kind=4), dict(rows_per_thread=3), dict(prefetch=8), dict(pass_kind=2, tile_y=6,
+        for bad in (dict(pass_kind=5), dict(rows_per_thread=3), dict(prefetch=8), dict(pass_kind=2, tile_y=6,
                                                                                    rows_per_thread=4),
                     dict(pass_kind=2, tile_y=64)):
             with pytest.raises(rs.RsfdError):
@@ -290,3 +290,57 @@ def test_seed_outside_the_energy_set(rs, prec, bound):
         assert (info["switches"] >= 1).all() and list(info["final_seed"]) == osw == [p.K + 1] * p.cols.size
         assert relf(G, Go) <= bound
         assert relf(G, Gref) <= max(bound, 1e-9)
+
+
+BFP_CASES = [((64, 18, 16), 4, 16, 16), ((40, 30, 17), 4, 8, 7), ((37, 26, 19), 4, 4, 19), ((48, 20, 15), 2, 16, 8),
+             ((33, 17, 13), 2, 8, 13)]
+
+
+@pytest.mark.parametrize("grid,order,tile_y,z_chunk", BFP_CASES)
+def test_block_floating_point_split_pass(rs, grid, order, tile_y, z_chunk):
+    """RSFD_PASS_SPLIT_BFP (leading parts of r_n on a per-column quantum, the product stored as s A r
+    with integer neighbour weights) on full and ragged tiles in x, y and z, 2nd and 4th order, with
+    seed switching: against the FP64 oracle, and against the plain split pass (the same iteration up
+    to double-float rounding: equal G0 within the double-float error, iteration counts within a few
+    per cent)."""
+    p = small_problem(grid=grid, h=0.4, fd_order=order, n_wells=6, n_energies=6, e_range=(-0.5, 0.5),
+                      eta=5e-2, tol=1e-10, cols=3, n_face=1)
+    outs = {}
+    for kind in (3, 4):
+        st, G, info, res, stats = gpu_g0(rs, p, rs.RSFD_DF64, opts=dict(pass_kind=kind, tile_y=tile_y,
+                                                                          z_chunk=z_chunk, slots=2))
+        assert st == rs.RSFD_OK
+        outs[kind] = (G, info["iters"].copy(), res)
+    Go, ores = shifted_cocg_columns(p, tol=1e-12)
+    assert max(r.switches for r in ores) >= 1
+    assert relf(outs[4][0], Go) <= 1e-6
+    assert relf(outs[4][0], outs[3][0]) <= 1e-6
+    assert (np.abs(outs[4][1] - outs[3][1]) <= 0.12 * outs[3][1] + 2).all()
+    assert (outs[4][2] < p.tol).all()
+
+
+def test_block_floating_point_kind_resolves_elsewhere(rs):
+    """FP64 and complex64 handles (and handles with projectors) run the plain split pass when asked for
+    the block-floating-point form: bit-identical results."""
+    p = small_problem(grid=(24, 14, 12), h=0.45, fd_order=4, n_wells=3, n_energies=4, e_range=(0.3, 2.0),
+                      eta=5e-2, tol=1e-10, cols=3)
+    for prec in (rs.RSFD_FP64, rs.RSFD_MIXED):
+        a = gpu_g0(rs, p, prec, opts=dict(pass_kind=3, slots=2), tol=1e-5 if prec == rs.RSFD_MIXED else None)
+        b = gpu_g0(rs, p, prec, opts=dict(pass_kind=4, slots=2), tol=1e-5 if prec == rs.RSFD_MIXED else None)
+        assert a[0] == b[0] == rs.RSFD_OK
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2]["iters"], b[2]["iters"])
+
+    # a double-float handle with projectors runs the plain split pass as well
+    pp = small_problem(grid=(24, 14, 12), h=0.45, fd_order=4, n_wells=3, n_energies=4, e_range=(0.3, 2.0),
+                       eta=5e-2, tol=1e-9, cols=3, projectors=3)
+    outs = []
+    for kind in (3, 4):
+        with rs.Handle(pp.grid, pp.h, pp.fd_order, pp.V, n_face=pp.n_face, proj=pp.proj,
+                       precision=rs.RSFD_DF64) as h:
+            rs.rsfd_set_solve_options(h.ptr, pass_kind=kind, slots=2)
+            G0 = torch.zeros((pp.K, pp.cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
+            st, info, res = rs.rsfd_shifted_cocg(h.ptr, pp.cols, pp.energies, pp.eta, pp.tol, pp.maxit, G0)
+            torch.cuda.synchronize()
+            assert st == rs.RSFD_OK
+            outs.append((G0.cpu().numpy(), info["iters"].copy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

@@ -42,7 +42,8 @@ def test_autotune_options_give_the_oracle_result(rs, prec):
     with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=getattr(rs, "RSFD_" + prec)) as h:
         opts, us = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=5, iters=64)
         assert us > 0
-        assert opts["pass_kind"] in (rs.RSFD_PASS_RECOMPUTE, rs.RSFD_PASS_STORED, rs.RSFD_PASS_SPLIT)
+        assert opts["pass_kind"] in (rs.RSFD_PASS_RECOMPUTE, rs.RSFD_PASS_STORED, rs.RSFD_PASS_SPLIT,
+                                     rs.RSFD_PASS_SPLIT_BFP)
         assert opts["slots"] == 5 and opts["iters_per_sync"] >= 1
         # a second call on the same shape is served from the cache
         opts2, us2 = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=5, iters=64)
