@@ -1736,8 +1736,9 @@ __device__ __forceinline__ void combine_body(const PassParams& p, const int slot
   }
 }
 
+// at most 64 registers: four CTAs (32 warps) per SM keep enough loads in flight for HBM
 template <int MODE, bool BFP>
-__global__ void __launch_bounds__(kCombThreads) combine_kernel(PassParams p) {
+__global__ void __launch_bounds__(kCombThreads, 4) combine_kernel(PassParams p) {
   combine_body<MODE, BFP>(p, blockIdx.y, blockIdx.x);
 }
 
@@ -2506,7 +2507,7 @@ int split_combine_ctas(int nz, int W, int sms) {
   // about eight 256-thread CTAs per SM over all slots, at least one plane each
   int c = (8 * sms + W - 1) / W;
   if (c > nz) c = nz;
-  if (c > 64) c = 64;
+  if (c > 256) c = 256;
   return c < 1 ? 1 : c;
 }
 int passu_box_x(int tile_x) { return passu_box_w(tile_x); }
