@@ -3,10 +3,11 @@ eta = 1e-3) in the launch configuration bench.py times, against stored oracle va
 
 bench.py solves blocks of 38 columns of this workload with double-float vectors, after letting the
 library's autotuner (rsfd_autotune, 256-iteration trial solves at 38 slots) choose the pass form
-and launch shape.  The first test goes through exactly that path; the second pins the launch shape
-the autotuner chose for the recorded benchmark run (stored pass, tile 32 x 16, one row per thread,
-z-chunk 128, 96-register variant), so that a timing-dependent pick can never leave the benchmarked
-shape without an oracle comparison.
+and launch shape.  The first test goes through exactly that path; the second pins the launch shapes
+the autotuner chose for recorded benchmark runs (the block-floating-point split pass with tile
+32 x 16, z-chunk 128, three planes in flight and the 64-register stencil; the plain split pass with
+the same tile; the stored pass with tile 32 x 16), so that a timing-dependent pick can never leave a
+benchmarked shape without an oracle comparison.
 
 The stored values (tests/golden/sampled_columns_mixed_golden.npz) are the FP64 CPU oracle's G0_bb
 at tolerance 1e-10 (and, when present, at the workload's 1e-6) on every 64th boundary row of the
@@ -26,7 +27,10 @@ from workloads import make_problem   # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sampled_columns_mixed_golden.npz")
 BENCH_COLS = 38          # columns per step of bench.py (four full CTA waves of the tuned shape)
-BENCH_SHAPE = dict(pass_kind=2, tile_y=16, rows_per_thread=1, z_chunk=128, tile_x=32, reg_budget=0)
+BENCH_SHAPES = [dict(pass_kind=4, tile_y=16, z_chunk=128, prefetch=3, reg_budget=1),
+                dict(pass_kind=3, tile_y=16, z_chunk=128, prefetch=3),
+                dict(pass_kind=2, tile_y=16, rows_per_thread=1, z_chunk=128, tile_x=32, reg_budget=0)]
+BENCH_SHAPE = BENCH_SHAPES[0]
 
 
 @pytest.fixture(scope="module")
@@ -91,11 +95,12 @@ def test_bench_path_autotuned_matches_stored_oracle(rs):
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="stored oracle values not generated")
-def test_recorded_bench_shape_matches_stored_oracle(rs):
-    """The launch shape of the recorded benchmark run, set explicitly, at 38 slots."""
+@pytest.mark.parametrize("shape", BENCH_SHAPES, ids=["split_bfp", "split", "stored"])
+def test_recorded_bench_shape_matches_stored_oracle(rs, shape):
+    """A launch shape of a recorded benchmark run, set explicitly, at 38 slots."""
     p = make_problem("sampled_columns_mixed")
     g = np.load(GOLDEN)
     batch = p.cols[:BENCH_COLS]
     with rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=rs.RSFD_DF64) as h:
-        rs.rsfd_set_solve_options(h.ptr, slots=BENCH_COLS, **BENCH_SHAPE)
+        rs.rsfd_set_solve_options(h.ptr, slots=BENCH_COLS, **shape)
         _check_against_golden(rs, h, p, batch, g)
