@@ -756,11 +756,13 @@ def run_uneven_regions(args):
     probs = make_problem("uneven_regions")
     ncols = args.ncols or 8
     prec = {"mixed": rs.RSFD_MIXED, "fp64": rs.RSFD_FP64, "df64": rs.RSFD_DF64}[args.precision]
-    hs, outs, cols, tuned = [], [], [], []
+    hs, outs, cols, tuned, topts = [], [], [], [], []
     for p in probs:
         h = rs.Handle(p.grid, p.h, p.fd_order, p.V, n_face=p.n_face, precision=prec)
-        c = p.cols[:ncols]
-        opts, us = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(c.size), iters=128)
+        # --full-columns: the configured columns (every plane point where 2 Nx Ny <= 4096, else 512 sampled)
+        c = p.cols if args.full_columns else p.cols[:ncols]
+        opts, us = rs.rsfd_autotune(h.ptr, p.energies, p.eta, slots=int(min(c.size, 256)), iters=128)
+        topts.append(opts)
         tuned.append({"region": p.name, "grid": list(p.grid), "K": int(p.K), "eta": p.eta, "us_per_slot_iteration": us,
                       "pass_kind": opts["pass_kind"], "tile_y": opts["tile_y"], "rows_per_thread": opts["rows_per_thread"],
                       "z_chunk": opts["z_chunk"]})
@@ -768,25 +770,41 @@ def run_uneven_regions(args):
         cols.append(c)
         outs.append(torch.zeros((p.K, c.size, h.nb), dtype=h.complex_dtype, device="cuda"))
     units = float(sum(c.size * p.K for c, p in zip(cols, probs)))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    forms = []
     its = []
-    for p, h, c, o in zip(probs, hs, cols, outs):
-        st, info, res = rs.rsfd_shifted_cocg(h.ptr, c, p.energies, p.eta, p.tol, p.maxit, o)
-        its.append(float(info["iters"].mean()))
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+    if not args.full_columns:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p, h, c, o in zip(probs, hs, cols, outs):
+            st, info, res = rs.rsfd_shifted_cocg(h.ptr, c, p.energies, p.eta, p.tol, p.maxit, o)
+            its.append(float(info["iters"].mean()))
+        torch.cuda.synchronize()
+        forms.append(("region_after_region", time.perf_counter() - t0, None))
+    for h, o in zip(hs, topts):   # the tuned options, with per-launch event timing
+        rs.rsfd_set_solve_options(h.ptr, **dict(o, profile=1))
     jobs = [dict(h=h.ptr, cols=c, energies=p.energies, eta=p.eta, tol=p.tol, maxit=p.maxit, G0_bb=o)
             for p, h, c, o in zip(probs, hs, cols, outs)]
     t0 = time.perf_counter()
     st, per = rs.rsfd_shifted_cocg_regions(jobs)
     torch.cuda.synchronize()
     t_con = time.perf_counter() - t0
-    for form, t in (("region_after_region", t_seq), ("regions_in_one_call", t_con)):
+    # per region: device busy time of its passes and shift updates against its stream's span, and the
+    # average host gap per iteration chunk that this leaves
+    regions = []
+    for p, h, c in zip(probs, hs, cols):
+        s = rs.rsfd_get_stats(h.ptr)
+        busy = s["ms_pass"] + s["ms_shift"]
+        regions.append({"region": p.name, "grid": list(p.grid), "columns": int(c.size), "K": int(p.K), "eta": p.eta,
+                        "slots": s["slots"], "mean_seed_iterations": s["slot_iterations"] / max(1, c.size),
+                        "ms_stream": s["ms_total"], "ms_busy": busy, "chunks": s["n_shift"],
+                        "ms_gap_per_chunk": (s["ms_total"] - busy) / max(1, s["n_shift"])})
+    forms.append(("regions_in_one_call", t_con, regions))
+    for form, t, reg in forms:
         print(json.dumps({"experiment": "uneven_regions", "form": form, "precision": args.precision,
-                          "columns_per_region": ncols, "seconds": t, "columns_x_energies": units,
-                          "value": units / t, "unit": UNIT, "mean_seed_iterations": its,
-                          "status": int(st), "tuned": tuned if form == "regions_in_one_call" else None}), flush=True)
+                          "columns_per_region": [int(c.size) for c in cols], "seconds": t,
+                          "columns_x_energies": units, "value": units / t, "unit": UNIT,
+                          "mean_seed_iterations": its or None, "status": int(st),
+                          "regions": reg, "tuned": tuned if form == "regions_in_one_call" else None}), flush=True)
     for h in hs:
         h.close()
 
@@ -811,6 +829,8 @@ def main():
     ap.add_argument("--z-chunk", type=int, default=0)
     ap.add_argument("--reg-budget", type=int, default=0, help="with --no-autotune: the pass's register budget option")
     ap.add_argument("--ncols", type=int, default=0, help="use only the first n columns (quick runs)")
+    ap.add_argument("--full-columns", action="store_true",
+                    help="uneven_regions: every configured column of each region, the one-call form only")
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--iters-per-sync", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -2057,8 +2057,11 @@ template <> struct ProjAcc<RSFD_DF64> {
   }
 };
 
+// one block per (atom, slot); an atom has ~10^3 support points, so a small block keeps the per-block
+// reduction and ticket cheap against the gather
+constexpr int kProjThreads = 128;
 template <int MODE>
-__global__ void __launch_bounds__(256) proj_kernel(ProjParams q) {
+__global__ void __launch_bounds__(kProjThreads) proj_kernel(ProjParams q) {
   typedef typename Ops<MODE>::C C;
   typedef typename Ops<MODE>::VT VT;
   __shared__ ScalarShared S;
@@ -2079,7 +2082,17 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjParams q) {
   if (tid == 0) {
     const double2 c = make_double2(v2[0] * q.h3, v2[1] * q.h3);
     const double E = q.a_E[a];
-    q.pw[(size_t)slot * q.n_atoms + a] = make_double2(-E * c.x, -E * c.y);
+    const double2 wv = make_double2(-E * c.x, -E * c.y);
+    if (MODE == RSFD_DF64) {
+      // stored as a double-float pair (16 bytes, the same slot): the scatter applies it to every
+      // support point of the atom without converting it again
+      dfc wc;
+      wc.h = make_float2((float)wv.x, (float)wv.y);
+      wc.l = make_float2((float)(wv.x - (double)wc.h.x), (float)(wv.y - (double)wc.h.y));
+      *reinterpret_cast<dfc*>(q.pw + (size_t)slot * q.n_atoms + a) = wc;
+    } else {
+      q.pw[(size_t)slot * q.n_atoms + a] = wv;
+    }
     const double2 c2 = cmul(c, c);
     q.pcorr[(size_t)slot * q.n_atoms + a] = make_double2(E * c2.x / q.h3, E * c2.y / q.h3);
     __threadfence();
@@ -2135,12 +2148,10 @@ __global__ void __launch_bounds__(256) pscatter_kernel(ProjParams q) {
     if (MODE == RSFD_DF64) {
       const dfc u0 = *reinterpret_cast<const dfc*>(&u[gi]);
       DFAcc acc = dfacc_from(u0);
+      const dfc* wd = reinterpret_cast<const dfc*>(w);   // -E_a c_a as double-float pairs (proj_kernel)
       for (int e = q.t_ptr[s]; e < q.t_ptr[s + 1]; ++e) {
-        const double2 ww = w[q.t_atom[e]];
+        const dfc wc = wd[q.t_atom[e]];
         const float2 pf = *reinterpret_cast<const float2*>(&tv[e]);
-        dfc wc;
-        wc.h = make_float2((float)ww.x, (float)ww.y);
-        wc.l = make_float2((float)(ww.x - (double)wc.h.x), (float)(ww.y - (double)wc.h.y));
         dfr c;
         c.h = pf.x;
         c.l = pf.y;
@@ -2186,23 +2197,23 @@ struct ChunkParams {
 template <int MODE> struct XUpd;
 template <> struct XUpd<RSFD_MIXED> {
   typedef float2 X;
-  static __device__ __forceinline__ X upd(X x, double2 e, X p, float2 s) {
-    return Ops<RSFD_MIXED>::mac(Ops<RSFD_MIXED>::cplx(e), p, f2add(x, s));
+  static __device__ __forceinline__ X updc(X x, float2 e, X p, float2 s) {
+    return Ops<RSFD_MIXED>::mac(e, p, f2add(x, s));
   }
 };
 template <> struct XUpd<RSFD_FP64> {
   typedef double2 X;
-  static __device__ __forceinline__ X upd(X x, double2 e, X p, double2 s) {
+  static __device__ __forceinline__ X updc(X x, double2 e, X p, double2 s) {
     return Ops<RSFD_FP64>::mac(e, p, make_double2(x.x + s.x, x.y + s.y));
   }
 };
 template <> struct XUpd<RSFD_DF64> {
   typedef dfc X;
-  static __device__ __forceinline__ X upd(X x, double2 e, X p, float2 s) {
+  static __device__ __forceinline__ X updc(X x, const dfz& e, X p, float2 s) {
     dfc sd;
     sd.h = s;
     sd.l = make_float2(0.f, 0.f);
-    return Ops<RSFD_DF64>::mac(Ops<RSFD_DF64>::cplx(e), p, df_add(x, sd));
+    return Ops<RSFD_DF64>::mac(e, p, df_add(x, sd));
   }
 };
 
@@ -2241,41 +2252,60 @@ __global__ void __launch_bounds__(256) chunk_coef_kernel(ChunkParams p) {
 // Apply the collapsed update: a block owns kChunkRows boundary rows of one slot, stages those rows'
 // residual history once in shared memory (each thread its own row) and sweeps every energy,
 //   x <- x + e_x p + sum_l W_x[l] r_l,   p <- e_p p + sum_l W_p[l] r_l,
-// in the same summation order as a per-energy sweep.
+// in the same summation order as a per-energy sweep.  The weights and factors of kChunkE energies at
+// a time are staged in shared memory (every thread reads the same weight: a broadcast), the factors
+// already converted to the vector element's coefficient type.
 constexpr int kChunkRows = 128;
+constexpr int kChunkE = 16;
 template <int MODE>
 __global__ void __launch_bounds__(kChunkRows) chunk_apply_kernel(ChunkParams p) {
   typedef typename XUpd<MODE>::X X;
   typedef typename Ops<MODE>::HR HR;
+  typedef typename Ops<MODE>::Cplx Cplx;
   typedef HOps<HR> HO;
   typedef typename HO::H H;
   extern __shared__ unsigned char chunk_smem[];
   const SolveDims& d = p.d;
   const int slot = blockIdx.y;
   const int hc = p.slots[slot].hcnt;
-  if (hc <= 0) return;
+  if (hc <= 0) return;   // uniform over the block
   const int tid = threadIdx.x, row = blockIdx.x * kChunkRows + tid;
-  if (row >= d.nb) return;   // no barrier below: every thread works on its own row only
-  H* hs = reinterpret_cast<H*>(chunk_smem);
+  const bool act = row < d.nb;
+  H* hs = reinterpret_cast<H*>(chunk_smem);                    // [hist_len][kChunkRows]
+  H* ws = hs + (size_t)p.hist_len * kChunkRows;                // [kChunkE][2][hist_len]
+  Cplx* es = reinterpret_cast<Cplx*>(ws + (size_t)kChunkE * 2 * p.hist_len);   // [kChunkE][2]
   const H* h = reinterpret_cast<const H*>(p.rhist) + (size_t)slot * p.hist_len * d.nb;
-  for (int l = 0; l < hc; ++l) hs[l * kChunkRows + tid] = h[(size_t)l * d.nb + row];
+  if (act)
+    for (int l = 0; l < hc; ++l) hs[l * kChunkRows + tid] = h[(size_t)l * d.nb + row];
   const H* W = reinterpret_cast<const H*>(p.wbuf) + (size_t)slot * d.K * 2 * p.hist_len;
   const double2* E = p.ebuf + (size_t)slot * d.K * 2;
   X* x = reinterpret_cast<X*>(p.xbuf) + (size_t)slot * d.K * d.nb + row;
   X* pp = reinterpret_cast<X*>(p.pbuf) + (size_t)slot * d.K * d.nb + row;
-  for (int i = 0; i < d.K; ++i) {
-    const H* Wx = W + (size_t)i * 2 * p.hist_len;
-    const H* Wp = Wx + p.hist_len;
-    H sx = HO::zero(), sp = HO::zero();
-    for (int l = 0; l < hc; ++l) {
-      const H r = hs[l * kChunkRows + tid];
-      sx = HO::mac(Wx[l], r, sx);
-      sp = HO::mac(Wp[l], r, sp);
+  for (int i0 = 0; i0 < d.K; i0 += kChunkE) {
+    const int ne = min(kChunkE, d.K - i0);
+    __syncthreads();   // the previous batch's weights are no longer read
+    for (int t = tid; t < ne * 2 * hc; t += kChunkRows) {
+      const int ii = t / (2 * hc), rem = t - ii * 2 * hc;
+      const int which = rem / hc, l = rem - which * hc;
+      ws[(ii * 2 + which) * p.hist_len + l] = W[((size_t)(i0 + ii) * 2 + which) * p.hist_len + l];
     }
-    const size_t o = (size_t)i * d.nb;
-    const X xo = x[o], po = pp[o];
-    x[o] = XUpd<MODE>::upd(xo, E[2 * i], po, sx);
-    pp[o] = XUpd<MODE>::upd(X(), E[2 * i + 1], po, sp);
+    for (int t = tid; t < ne * 2; t += kChunkRows) es[t] = Ops<MODE>::cplx(E[2 * i0 + t]);
+    __syncthreads();
+    if (!act) continue;
+    for (int ii = 0; ii < ne; ++ii) {
+      const H* Wx = ws + (size_t)ii * 2 * p.hist_len;
+      const H* Wp = Wx + p.hist_len;
+      H sx = HO::zero(), sp = HO::zero();
+      for (int l = 0; l < hc; ++l) {
+        const H r = hs[l * kChunkRows + tid];
+        sx = HO::mac(Wx[l], r, sx);
+        sp = HO::mac(Wp[l], r, sp);
+      }
+      const size_t o = (size_t)(i0 + ii) * d.nb;
+      const X xo = x[o], po = pp[o];
+      x[o] = XUpd<MODE>::updc(xo, es[2 * ii], po, sx);
+      pp[o] = XUpd<MODE>::updc(X(), es[2 * ii + 1], po, sp);
+    }
   }
 }
 
@@ -2644,7 +2674,7 @@ cudaError_t launch_proj_t(const SolveDims& d, const SolverBuffers& b, const Sten
   q.pw = b.pw;
   q.pcorr = b.pcorr;
   q.ptickets = b.ptickets;
-  proj_kernel<MODE><<<dim3(b.n_atoms, d.W), 256, 0, st>>>(q);
+  proj_kernel<MODE><<<dim3(b.n_atoms, d.W), kProjThreads, 0, st>>>(q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int gx = (b.n_supp + 255) / 256;
@@ -2679,7 +2709,9 @@ cudaError_t launch_chunk(int prec, const SolveDims& d, const SolverBuffers& b, i
   p.ebuf = b.cebuf;
   const int nct = (d.W * d.K + 255) / 256;
   dim3 grid((d.nb + kChunkRows - 1) / kChunkRows, d.W);
-  const size_t smem = (size_t)hist_len * kChunkRows * (prec == RSFD_FP64 ? 16 : 8);
+  const size_t hsz = prec == RSFD_FP64 ? 16 : 8;            // history / weight element
+  const size_t csz = prec == RSFD_MIXED ? 8 : 16;           // converted factor (float2, double2, dfz)
+  const size_t smem = (size_t)hist_len * kChunkRows * hsz + (size_t)kChunkE * 2 * hist_len * hsz + kChunkE * 2 * csz;
   if (prec == RSFD_FP64) {
     chunk_coef_kernel<RSFD_FP64><<<nct, 256, 0, st>>>(p);
     chunk_apply_kernel<RSFD_FP64><<<grid, kChunkRows, smem, st>>>(p);

@@ -174,7 +174,7 @@ struct SolverBuffers {
   const int* t_atom;      // [nnz] atom of each point-major entry
   const void* t_val;      // [nnz] its projector value
   double h3;
-  double2* pw;            // [W][n_atoms] -E_a c_a of the last pass
+  double2* pw;            // [W][n_atoms] -E_a c_a of the last pass (double-float handles: as a (hi, lo) float pair)
   double2* pcorr;         // [W][n_atoms] E_a c_a^2 / h^3
   double* pdots;          // [W][8] (r,r), (r, u_loc), ||r||^2 of the last pass
   unsigned int* ptickets; // [W]
