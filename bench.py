@@ -791,13 +791,17 @@ def run_uneven_regions(args):
     # per region: device busy time of its passes and shift updates against its stream's span, and the
     # average host gap per iteration chunk that this leaves
     regions = []
-    for p, h, c in zip(probs, hs, cols):
+    for p, h, c, (rst, rinfo, _) in zip(probs, hs, cols, per):
         s = rs.rsfd_get_stats(h.ptr)
         busy = s["ms_pass"] + s["ms_shift"]
+        # ms_stream - ms_busy: the region's stream waiting, on the host between chunks or behind the
+        # other regions' kernels on the shared SMs
         regions.append({"region": p.name, "grid": list(p.grid), "columns": int(c.size), "K": int(p.K), "eta": p.eta,
                         "slots": s["slots"], "mean_seed_iterations": s["slot_iterations"] / max(1, c.size),
+                        "status": int(rst), "columns_not_converged": int((rinfo["status"] != 0).sum()),
+                        "max_seed_iterations": int(rinfo["iters"].max()) if rinfo.size else 0,
                         "ms_stream": s["ms_total"], "ms_busy": busy, "chunks": s["n_shift"],
-                        "ms_gap_per_chunk": (s["ms_total"] - busy) / max(1, s["n_shift"])})
+                        "ms_wait_per_chunk": (s["ms_total"] - busy) / max(1, s["n_shift"])})
     forms.append(("regions_in_one_call", t_con, regions))
     for form, t, reg in forms:
         print(json.dumps({"experiment": "uneven_regions", "form": form, "precision": args.precision,

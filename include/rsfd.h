@@ -109,7 +109,8 @@ typedef struct {
 
 /* Form of the seed iteration's pass (rsfd_solve_opts.pass_kind). */
 typedef enum {
-  RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED (measured faster in every precision on the 64^2 x 128 workload) */
+  RSFD_PASS_AUTO = 0,      /* RSFD_PASS_STORED when the options are not tuned; rsfd_autotune times every form
+                              (on the 64^2 x 128 workload it picks RSFD_PASS_SPLIT_BFP for double-float) */
   RSFD_PASS_RECOMPUTE = 1, /* three vectors per iteration (r_{n-1}, r_{n-2} in, r_n out); A r_{n-1} is
                               recomputed on the tile plus halo and A r_n again for the dot products */
   RSFD_PASS_STORED = 2,    /* five vectors per iteration (r_{n-1}, r_{n-2}, A r_{n-1} in; r_n, A r_n out);

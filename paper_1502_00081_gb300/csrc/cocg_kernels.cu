@@ -1736,13 +1736,10 @@ __device__ __forceinline__ void combine_body(const PassParams& p, const int slot
   }
 }
 
-// At most 64 registers: four CTAs (32 warps) per SM keep enough loads in flight for HBM.  The slots
-// run in reverse order (the stencil launches run them forward), so the combine starts on the slots
-// whose r_{n-1} and A r_{n-1} the preceding stencil launch touched last and may still find in L2,
-// and the following stencil starts on the slots whose r_n the combine wrote last.
+// At most 64 registers: four CTAs (32 warps) per SM keep enough loads in flight for HBM.
 template <int MODE, bool BFP>
 __global__ void __launch_bounds__(kCombThreads, 4) combine_kernel(PassParams p) {
-  combine_body<MODE, BFP>(p, (int)gridDim.y - 1 - (int)blockIdx.y, blockIdx.x);
+  combine_body<MODE, BFP>(p, blockIdx.y, blockIdx.x);
 }
 
 // Stencil: CTA = a 32 x TY tile of one slot and a z-range, one thread per tile point (one warp per
