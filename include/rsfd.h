@@ -118,15 +118,17 @@ typedef enum {
   RSFD_PASS_SPLIT = 3,     /* the stored-product iteration as two launches: a pointwise combine (r_n from
                               r_{n-1}, r_{n-2}, A r_{n-1}; four vectors) and a stencil (A r_n from r_n; two
                               vectors plus its halo); one row per thread, tile width 32, tile_y <= 16 */
-  RSFD_PASS_SPLIT_BFP = 4  /* double-float handles without projectors: RSFD_PASS_SPLIT with the leading
+  RSFD_PASS_SPLIT_BFP = 4  /* double-float handles: RSFD_PASS_SPLIT with the leading
                               parts of r_n rounded to a per-column, per-iteration quantum q (block floating
                               point, q chosen from a bound on |r_n| so that every leading part is at most
                               2^21 q) and the product stored as s A r
                               with s = 24 h^2 (4th order) or 2 h^2 (2nd order), which makes the neighbour
                               weights the integers 16, -1 (or 1): the stencil's neighbour sums of leading
                               parts are then exact FP32 additions.  The iterates agree with RSFD_PASS_SPLIT
-                              to double-float rounding (about 2^-45 of the bound on |r_n|);
-                              other handles run RSFD_PASS_SPLIT */
+                              to double-float rounding (about 2^-45 of the bound on |r_n|).  With
+                              projectors the bound adds (atoms per support point) x max_a |s E_a c_a|
+                              max|p_a| for the projector term.  FP64 and complex64 handles run
+                              RSFD_PASS_SPLIT */
 } rsfd_pass_kind;
 
 /* Form of the Dyson solve (rsfd_solve_opts.dyson_kind). */

@@ -1263,6 +1263,8 @@ __global__ void __launch_bounds__(MaxThreads<MODE>::value) pass_kernel(PassParam
         o[2] = S.rAr.x;
         o[3] = S.rAr.y;
         o[4] = S.nrm2;
+        o[5] = S.maxr;   // block-floating-point bounds (zero for the other forms)
+        o[6] = S.maxu;
       }
     } else {
       scalar_step(p, slot, S);
@@ -1596,6 +1598,8 @@ __global__ void __launch_bounds__(NT) passu_kernel(PassParams p, const __grid_co
         o[2] = S.rAr.x;
         o[3] = S.rAr.y;
         o[4] = S.nrm2;
+        o[5] = S.maxr;   // block-floating-point bounds (zero for the other forms)
+        o[6] = S.maxu;
       }
     } else {
       scalar_step(p, slot, S);
@@ -1982,6 +1986,8 @@ __device__ __forceinline__ void stencil_body(const PassParams& p, const CUtensor
         o[2] = S.rAr.x;
         o[3] = S.rAr.y;
         o[4] = S.nrm2;
+        o[5] = S.maxr;   // block-floating-point bounds (zero for the other forms)
+        o[6] = S.maxu;
       }
     } else {
       scalar_step(p, slot, S);
@@ -2021,6 +2027,8 @@ struct ProjParams {
   double2* pw;
   double2* pcorr;
   unsigned int* ptickets;
+  const double* pmax;        // per atom: largest |projector value|
+  int overlap;               // largest number of atoms at one support point
 };
 
 // per-thread FP64 sum of p_j r_j, per precision
@@ -2079,7 +2087,8 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(ProjParams q) {
   if (tid == 0) {
     const double2 c = make_double2(v2[0] * q.h3, v2[1] * q.h3);
     const double E = q.a_E[a];
-    const double2 wv = make_double2(-E * c.x, -E * c.y);
+    const double us = p.uscale;   // the block-floating-point pass stores s A r
+    const double2 wv = make_double2(-E * us * c.x, -E * us * c.y);
     if (MODE == RSFD_DF64) {
       // stored as a double-float pair (16 bytes, the same slot): the scatter applies it to every
       // support point of the atom without converting it again
@@ -2109,11 +2118,24 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(ProjParams q) {
     }
     cx = warp_sum(cx);
     cy = warp_sum(cy);
+    // block-floating-point bound: |components of sum_a w_a p_a| at any point is at most (atoms at a
+    // support point) x max_a (|Re w_a| + |Im w_a|) max|p_a|
+    double wm = 0.0;
+    if (MODE == RSFD_DF64 && p.bfp) {
+      const dfc* wd = reinterpret_cast<const dfc*>(q.pw + (size_t)slot * q.n_atoms);
+      for (int k = tid; k < q.n_atoms; k += 32) {
+        const float2 wh = __ldcg(&wd[k].h);
+        wm = fmax(wm, ((double)fabsf(wh.x) + (double)fabsf(wh.y)) * q.pmax[k]);
+      }
+      for (int o = 16; o > 0; o >>= 1) wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    }
     if (tid == 0) {
       const double* dd = p.pdots + (size_t)slot * 8;
       S.rr = make_double2(__ldcg(dd + 0), __ldcg(dd + 1));
       S.rAr = make_double2(__ldcg(dd + 2) - cx, __ldcg(dd + 3) - cy);
       S.nrm2 = __ldcg(dd + 4);
+      S.maxr = __ldcg(dd + 5);
+      S.maxu = __ldcg(dd + 6) + (double)q.overlap * wm;
       q.ptickets[slot] = 0u;
     }
   }
@@ -2652,10 +2674,10 @@ cudaError_t launch_proj_t(const SolveDims& d, const SolverBuffers& b, const Sten
   p.depth = d.depth;
   p.stored_u = 1;
   p.has_proj = 1;
-  p.bfp = 0;   // the block-floating-point form has no projector term
+  p.bfp = (MODE == RSFD_DF64 && d.kind == RSFD_PASS_SPLIT_BFP) ? 1 : 0;
   p.kb = 21;
-  p.uscale = 1.0;
-  p.Vs = nullptr;
+  p.uscale = p.bfp ? b.uscale : 1.0;
+  p.Vs = b.Vs;
   p.pdots = b.pdots;
   q.n_atoms = b.n_atoms;
   q.n_supp = b.n_supp;
@@ -2671,6 +2693,8 @@ cudaError_t launch_proj_t(const SolveDims& d, const SolverBuffers& b, const Sten
   q.pw = b.pw;
   q.pcorr = b.pcorr;
   q.ptickets = b.ptickets;
+  q.pmax = b.a_pmax;
+  q.overlap = b.proj_overlap;
   proj_kernel<MODE><<<dim3(b.n_atoms, d.W), kProjThreads, 0, st>>>(q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -58,6 +58,8 @@ struct Handle {
   long long *d_aidx = nullptr, *d_tpidx = nullptr;
   void *d_aval = nullptr, *d_tval = nullptr;
   double* d_aE = nullptr;
+  double* d_pmax = nullptr;    // per atom: the largest |projector value| (the block-floating-point bound)
+  int proj_overlap = 0;        // largest number of atoms sharing a support point
   uint64_t in_hash = 0;        // hash of the operator's inputs (grid, h, order, faces, precision, V, projectors)
   DevBuf sweep;                // one column block of G0_bb for rsfd_shifted_cocg_sweep
   rsfd_solve_opts opts;
@@ -160,13 +162,14 @@ static void free_all(Handle* h) {
   if (h->dV) cudaFree(h->dV);
   if (h->dVs) cudaFree(h->dVs);
   if (h->dbrow) cudaFree(h->dbrow);
-  void* pj[] = {h->d_aptr, h->d_tptr, h->d_tatom, h->d_aidx, h->d_tpidx, h->d_aval, h->d_tval, h->d_aE};
+  void* pj[] = {h->d_aptr, h->d_tptr, h->d_tatom, h->d_aidx, h->d_tpidx, h->d_aval, h->d_tval, h->d_aE, h->d_pmax};
   for (void* q : pj)
     if (q) cudaFree(q);
   h->d_aptr = h->d_tptr = h->d_tatom = nullptr;
   h->d_aidx = h->d_tpidx = nullptr;
   h->d_aval = h->d_tval = nullptr;
   h->d_aE = nullptr;
+  h->d_pmax = nullptr;
   h->dV = nullptr;
   h->dVs = nullptr;
   h->dbrow = nullptr;
@@ -246,10 +249,9 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
   return RSFD_OK;
 }
 
-// the block-floating-point split pass serves double-float handles without projectors; the others
-// run the plain split pass
-static int resolve_kind(int prec, int opt, int n_atoms = 0) {
-  if (opt == RSFD_PASS_SPLIT_BFP) return (prec == RSFD_DF64 && n_atoms == 0) ? opt : RSFD_PASS_SPLIT;
+// the block-floating-point split pass serves double-float handles; the others run the plain split pass
+static int resolve_kind(int prec, int opt, int = 0) {
+  if (opt == RSFD_PASS_SPLIT_BFP) return prec == RSFD_DF64 ? opt : RSFD_PASS_SPLIT;
   if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED || opt == RSFD_PASS_SPLIT) return opt;
   return RSFD_PASS_STORED;
 }
@@ -508,6 +510,11 @@ static rsfd_status rsfd_create_impl(rsfd_handle* out, const int32_t grid[3], dou
       put(tval, k, proj->val[e2]);
     }
     tptr.push_back((int)nnz);
+    std::vector<double> pmax(na, 0.0);
+    for (int a = 0; a < na; ++a)
+      for (long long e2 = proj->ptr[a]; e2 < proj->ptr[a + 1]; ++e2) pmax[a] = std::max(pmax[a], std::fabs(proj->val[e2]));
+    h->proj_overlap = 0;
+    for (size_t k = 0; k + 1 < tptr.size(); ++k) h->proj_overlap = std::max(h->proj_overlap, tptr[k + 1] - tptr[k]);
     h->n_atoms = na;
     h->nnz = nnz;
     h->n_supp = (int)tpidx.size();
@@ -519,6 +526,7 @@ static rsfd_status rsfd_create_impl(rsfd_handle* out, const int32_t grid[3], dou
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tpidx, (tpidx.size() + 1) * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tatom, (nnz + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_tval, nnz * vsz + 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_pmax, na * sizeof(double));
     if (e != cudaSuccess) return bail(RSFD_ERR_ALLOC, std::string("rsfd_create: ") + cudaGetErrorString(e));
     e = cudaMemcpy(h->d_aptr, aptr.data(), (na + 1) * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_aidx, aidx.data(), nnz * sizeof(long long), cudaMemcpyHostToDevice);
@@ -529,6 +537,7 @@ static rsfd_status rsfd_create_impl(rsfd_handle* out, const int32_t grid[3], dou
       e = cudaMemcpy(h->d_tpidx, tpidx.data(), tpidx.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_tatom, tatom.data(), nnz * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_tval, tval.data(), nnz * vsz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_pmax, pmax.data(), na * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(RSFD_ERR_CUDA, std::string("rsfd_create: ") + cudaGetErrorString(e));
   }
   *out = h;
@@ -810,6 +819,8 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
     b.a_val = h->d_aval;
     b.a_E = h->d_aE;
     b.t_ptr = h->d_tptr;
+    b.a_pmax = h->d_pmax;
+    b.proj_overlap = h->proj_overlap;
     b.t_pidx = h->d_tpidx;
     b.t_atom = h->d_tatom;
     b.t_val = h->d_tval;

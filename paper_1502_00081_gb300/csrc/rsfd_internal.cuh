@@ -173,6 +173,8 @@ struct SolverBuffers {
   const long long* t_pidx;// [n_supp] padded vector index of each support point
   const int* t_atom;      // [nnz] atom of each point-major entry
   const void* t_val;      // [nnz] its projector value
+  const double* a_pmax;   // [n_atoms] largest |projector value| of each atom
+  int proj_overlap;       // largest number of atoms at one support point
   double h3;
   double2* pw;            // [W][n_atoms] -E_a c_a of the last pass (double-float handles: as a (hi, lo) float pair)
   double2* pcorr;         // [W][n_atoms] E_a c_a^2 / h^3

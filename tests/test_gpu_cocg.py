@@ -320,8 +320,8 @@ def test_block_floating_point_split_pass(rs, grid, order, tile_y, z_chunk):
 
 
 def test_block_floating_point_kind_resolves_elsewhere(rs):
-    """FP64 and complex64 handles (and handles with projectors) run the plain split pass when asked for
-    the block-floating-point form: bit-identical results."""
+    """FP64 and complex64 handles run the plain split pass when asked for the block-floating-point
+    form: bit-identical results."""
     p = small_problem(grid=(24, 14, 12), h=0.45, fd_order=4, n_wells=3, n_energies=4, e_range=(0.3, 2.0),
                       eta=5e-2, tol=1e-10, cols=3)
     for prec in (rs.RSFD_FP64, rs.RSFD_MIXED):
@@ -329,18 +329,3 @@ def test_block_floating_point_kind_resolves_elsewhere(rs):
         b = gpu_g0(rs, p, prec, opts=dict(pass_kind=4, slots=2), tol=1e-5 if prec == rs.RSFD_MIXED else None)
         assert a[0] == b[0] == rs.RSFD_OK
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2]["iters"], b[2]["iters"])
-
-    # a double-float handle with projectors runs the plain split pass as well
-    pp = small_problem(grid=(24, 14, 12), h=0.45, fd_order=4, n_wells=3, n_energies=4, e_range=(0.3, 2.0),
-                       eta=5e-2, tol=1e-9, cols=3, projectors=3)
-    outs = []
-    for kind in (3, 4):
-        with rs.Handle(pp.grid, pp.h, pp.fd_order, pp.V, n_face=pp.n_face, proj=pp.proj,
-                       precision=rs.RSFD_DF64) as h:
-            rs.rsfd_set_solve_options(h.ptr, pass_kind=kind, slots=2)
-            G0 = torch.zeros((pp.K, pp.cols.size, h.nb), dtype=h.complex_dtype, device="cuda")
-            st, info, res = rs.rsfd_shifted_cocg(h.ptr, pp.cols, pp.energies, pp.eta, pp.tol, pp.maxit, G0)
-            torch.cuda.synchronize()
-            assert st == rs.RSFD_OK
-            outs.append((G0.cpu().numpy(), info["iters"].copy()))
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

@@ -102,7 +102,8 @@ def peapod_oracle():
     return p, cols, Go
 
 
-@pytest.mark.parametrize("prec,bound,kind", [("FP64", 1e-10, 2), ("DF64", 1e-6, 2), ("DF64", 1e-6, 3)])
+@pytest.mark.parametrize("prec,bound,kind", [("FP64", 1e-10, 2), ("DF64", 1e-6, 2), ("DF64", 1e-6, 3),
+                                              ("DF64", 1e-6, 4)])
 def test_peapod_full_size_first_iterations_match_oracle(rs, peapod_oracle, prec, bound, kind):
     """The 72 x 72 x 256 peapod-shaped workload (460 wells + 460 KB projectors, 100 energies): the
     boundary rows of x^(i) after 40 iterations for two sampled columns equal the oracle's."""
@@ -111,3 +112,22 @@ def test_peapod_full_size_first_iterations_match_oracle(rs, peapod_oracle, prec,
     assert st == rs.RSFD_ERR_NOT_CONVERGED
     assert (info["iters"] == 40).all()
     assert relf(G, Go) <= bound
+
+
+@pytest.mark.parametrize("grid,order,tile_y", [((37, 21, 20), 4, 8), ((40, 18, 17), 4, 16), ((33, 20, 16), 2, 8)])
+def test_projectors_block_floating_point_pass(rs, grid, order, tile_y):
+    """The block-floating-point split pass with projectors (its bound on |s A r| includes the projector
+    term: atoms per support point x the largest |s E_a c_a| max|p_a|): ragged tiles, overlapping
+    supports, seed switching, against the oracle's converged G0 and the plain split pass."""
+    p = small_problem(grid=grid, h=0.45, fd_order=order, n_wells=3, projectors=6, n_energies=5,
+                      e_range=(0.5, 2.5), eta=5e-2, tol=1e-10, cols=5)
+    outs = {}
+    for kind in (3, 4):
+        st, G, info = gpu_g0(rs, p, rs.RSFD_DF64, p.cols, opts=dict(slots=3, tile_y=tile_y, pass_kind=kind))
+        assert st == rs.RSFD_OK
+        outs[kind] = (G, info["iters"].copy())
+    Go, res = shifted_cocg_columns(p, cols=p.cols, tol=1e-12)
+    assert max(r.switches for r in res) >= 1
+    assert relf(outs[4][0], Go) <= 1e-6
+    assert relf(outs[4][0], outs[3][0]) <= 1e-6
+    assert (np.abs(outs[4][1] - outs[3][1]) <= 0.12 * outs[3][1] + 2).all()
