@@ -202,9 +202,10 @@ typedef struct {
  *               0 selects fd_order/2 (the planes the lead couples to).
  *   V_loc     = host [N] local potential, linear grid order.
  *   proj      = NULL or the nonlocal projectors (host arrays, copied; entries of one atom at distinct
- *               grid points).  With projectors the solver always uses the stored-product pass: after
- *               each pass a projection kernel forms c_a = h^3 p_a^T r_n, corrects (r_n, A r_n) and runs
- *               the scalar step, and a scatter kernel adds -sum_a E_a c_a p_a to A r_n.
+ *               grid points).  With projectors the solver uses a pass that stores A r (the
+ *               stored-product pass or a split pass; RSFD_PASS_RECOMPUTE becomes RSFD_PASS_STORED):
+ *               after each pass a projection kernel forms c_a = h^3 p_a^T r_n, corrects (r_n, A r_n)
+ *               and runs the scalar step, and a scatter kernel adds -sum_a E_a c_a p_a to A r_n.
  *   precision = RSFD_FP64, RSFD_MIXED or RSFD_DF64.
  *   stream    = cudaStream_t for every device operation of this handle.
  * Returns RSFD_ERR_ARG on invalid sizes, RSFD_ERR_ALLOC / RSFD_ERR_CUDA on

@@ -250,7 +250,7 @@ static rsfd_status make_maps(Handle* h, int W, int tile_y, int kind, int tile_x)
 }
 
 // the block-floating-point split pass serves double-float handles; the others run the plain split pass
-static int resolve_kind(int prec, int opt, int = 0) {
+static int resolve_kind(int prec, int opt) {
   if (opt == RSFD_PASS_SPLIT_BFP) return prec == RSFD_DF64 ? opt : RSFD_PASS_SPLIT;
   if (opt == RSFD_PASS_RECOMPUTE || opt == RSFD_PASS_STORED || opt == RSFD_PASS_SPLIT) return opt;
   return RSFD_PASS_STORED;
@@ -599,7 +599,7 @@ static rsfd_status rsfd_set_solve_options_impl(rsfd_handle h, const rsfd_solve_o
   const int rows = resolve_rows(o->rows_per_thread);
   if (o->prefetch > pass_max_depth())
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: prefetch must be <= " + std::to_string(pass_max_depth()));
-  const int kind = resolve_kind(h->prec, o->pass_kind, h->n_atoms);
+  const int kind = resolve_kind(h->prec, o->pass_kind);
   if (o->reg_budget < 0 || o->reg_budget > 1)
     return fail(h, RSFD_ERR_ARG, "rsfd_set_solve_options: reg_budget must be 0 or 1");
   if (o->tile_x != 0 && o->tile_x != 16 && o->tile_x != 32)
@@ -688,7 +688,7 @@ static rsfd_status rsfd_shifted_cocg_impl(rsfd_handle h, const int64_t* cols, in
   d.K = K;
   d.kreq = Kout;
   d.ncols = ncols;
-  d.kind = resolve_kind(prec, h->opts.pass_kind, h->n_atoms);
+  d.kind = resolve_kind(prec, h->opts.pass_kind);
   // the projector term follows a pass that stores A r (stored-product or split)
   if (h->n_atoms > 0 && d.kind == RSFD_PASS_RECOMPUTE) d.kind = RSFD_PASS_STORED;
   d.nvec = d.kind == RSFD_PASS_RECOMPUTE ? 3 : 5;
@@ -1181,7 +1181,7 @@ static rsfd_status rsfd_autotune_impl(rsfd_handle h, const double* energies, int
   const int kinds[4] = {RSFD_PASS_STORED, RSFD_PASS_RECOMPUTE, RSFD_PASS_SPLIT, RSFD_PASS_SPLIT_BFP};
   const int zcs[3] = {0, h->nz, (h->nz + 1) / 2};
   for (int kind : kinds) {
-    if (kind == RSFD_PASS_SPLIT_BFP && resolve_kind(h->prec, kind, h->n_atoms) != kind) continue;
+    if (kind == RSFD_PASS_SPLIT_BFP && resolve_kind(h->prec, kind) != kind) continue;
     if (is_split(kind)) {
       // the split pass: tile height and z-chunk
       const int tys[3] = {8, 4, 16};
