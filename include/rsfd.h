@@ -160,8 +160,9 @@ typedef struct {
                              the pass, 0 = at most 96 (CTAs of <= 640 threads; two CTAs of <= 320 threads
                              per SM), 1 = at most 128 (CTAs of <= 512 threads, tile_y <= 14, one CTA per
                              SM, no register spills); RSFD_PASS_SPLIT_BFP: the stencil launch keeps 0 = at
-                             most 96 (one 512-thread CTA per SM) or 1 = at most 64 registers (two); other
-                             passes ignore it */
+                             most 128 / 85 registers (one 512-thread or three 256-thread CTAs per SM) or
+                             1 = at most 64 (two 512-thread or four 256-thread CTAs per SM); other passes
+                             ignore it */
   int32_t tile_x;         /* RSFD_PASS_STORED, double-float, one row per thread: tile width in x, 0 or 32
                              (one tile row per warp) or 16 (two tile rows per warp; less idle work when Nx
                              is an odd multiple of 16, e.g. 48 or 80); tile_y must be even */
