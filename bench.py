@@ -184,6 +184,27 @@ def oracle_sample(p, budget_s=15.0):
     return dt / max(r.iterations, 1), r.iterations, dt
 
 
+def _oracle_worker(job):
+    """One host core's share of the all-cores oracle sample (a spawned process): the workload rebuilt
+    from its seed, one column, the same bounded sample as the single-core leg."""
+    name, col_index, budget_s = job
+    from workloads import make_problem
+    p = make_problem(name)
+    p.cols = np.asarray(p.cols)[[col_index % len(p.cols)]]
+    return oracle_sample(p, budget_s)
+
+
+def oracle_all_cores(p, budget_s, ncores=None):
+    """The oracle as it stands on every host core at once: one spawned process per core, each timing its
+    own column (columns are independent).  Returns seed iterations per second summed over the cores,
+    the core count and the per-process samples."""
+    import multiprocessing as mp
+    n = int(ncores or os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_worker, [(p.name, i, budget_s) for i in range(n)])
+    return sum(1.0 / r[0] for r in res), n, res
+
+
 def _oracle_iterations_per_column(p):
     """Seed iterations per column of this workload, as stored by tests/golden/make_golden.py from
     the oracle itself (None when absent)."""
@@ -193,7 +214,7 @@ def _oracle_iterations_per_column(p):
     return None
 
 
-def cpu_baseline_line(p, budget_s, gpu_mean_iters=None):
+def cpu_baseline_line(p, budget_s, gpu_mean_iters=None, all_cores=False):
     t_it, n_it, dt = oracle_sample(p, budget_s)
     stored = _oracle_iterations_per_column(p)
     if stored is not None:
@@ -203,10 +224,17 @@ def cpu_baseline_line(p, budget_s, gpu_mean_iters=None):
     else:
         iters_per_col, src = float("nan"), "unknown"
     value = p.K / (t_it * iters_per_col)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    line = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"1 column x {p.K} energies, first {n_it} seed iterations ({dt:.1f} s, numpy/scipy "
                        f"single-threaded, host nproc={os.cpu_count()}), scaled to {iters_per_col:.0f} "
                        f"iterations per column ({src})")}
+    if all_cores:
+        rate, n, res = oracle_all_cores(p, budget_s)
+        line["all_cores"] = {"value": p.K * rate / iters_per_col, "unit": UNIT, "cores": n, "kind": "oracle",
+                             "sample": (f"{n} spawned processes, one column each, {min(r[1] for r in res)}-"
+                                        f"{max(r[1] for r in res)} seed iterations in about {budget_s:.0f} s "
+                                        f"each, iteration rates summed, scaled like the single-core figure")}
+    return line
 
 
 # ---------------------------------------------------------------------------------------------
@@ -372,7 +400,8 @@ def run_gpu(args):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_line(p, args.cpu_budget, gpu_mean_iters=statistics.mean(iters))
+        cpu = cpu_baseline_line(p, args.cpu_budget, gpu_mean_iters=statistics.mean(iters),
+                                all_cores=not args.no_cpu_all_cores)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -842,6 +871,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-option autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-all-cores", action="store_true",
+                    help="skip the all-cores oracle figure (one spawned process per host core)")
     ap.add_argument("--experiment", default=None,
                     choices=[None, "shift_scaling", "precision_speedup", "dyson_scaling", "tc_gemm",
                              "uneven_regions", "full_boundary"],
